@@ -1,0 +1,177 @@
+/*
+ * lbm.h -- C ABI of the B300 D2Q37 thermal lattice Boltzmann step.
+ *
+ * Method: Ripesi, Biferale, Schifano & Tripiccione, "Evolution of a double-front
+ * Rayleigh-Taylor system using a GPU-based high resolution thermal Lattice-Boltzmann
+ * model", Phys. Rev. E 89, 043022 (2014).  One time step is the lattice BGK update of
+ * Sec. III.A Eq. (LBE): pull-propagate of the 37 populations with periodic x
+ * (Sec. III.B, steps pbc and propagate), the top/bottom wall rule on rows 0..2 and
+ * Lz-3..Lz-1 (Sec. III.B, step bc) and the collide with the force-shifted equilibrium
+ * f^eq[rho, u + tau g, T + tau (1 - tau) g^2 / D] (Sec. III.A).
+ *
+ * Conventions shared by every entry point
+ *   - Lattice Lx x Lz sites; x periodic, z bounded by walls at z = -1/2 and Lz - 1/2.
+ *     Lx >= 1, Lz >= 6 and 37 * Lx * Lz < 2^31.
+ *   - Units: dt = 1, reference temperature 1, xi_l = r c_l (r ~ 1.1969, Sec. III.A),
+ *     gravity vector (0, -g) with g >= 0 (z points up, Sec. II Eq. (NS)).
+ *   - Population storage is structure-of-arrays, column-major (Sec. III.B):
+ *     element (l, x, z) at ((l * Lx) + x) * Lz + z, z fastest.  The canonical velocity
+ *     order is l = 0 for (0,0), then the shells |c|^2 = 1,2,4,5,8,9,10, each sorted by
+ *     the polar angle atan2(c_z, c_x) in [0, 2 pi).
+ *   - Wall rule (Sec. III.B names the rows, not the rule; this library's reading):
+ *     half-way bounce-back on the same column: a pull source row z - c_z below 0 is
+ *     replaced by population opp(l) at row c_z - 1 - z, one at or above Lz by opp(l) at
+ *     row 2 Lz - 1 - z + c_z.  Propagate + bc is then a permutation of (l, x, z).
+ *   - Device pointers are CUDA device addresses on the context's device; host
+ *     pointers are ordinary host memory.  Buffers passed in are BORROWED: the caller
+ *     (e.g. PyTorch) owns them and must keep them alive until lbm_destroy.
+ *   - Calls are asynchronous on the context's stream unless stated.  Kernel-side
+ *     errors surface at the next synchronising call (lbm_sync, or any call that
+ *     copies to the host).
+ *   - Every int-returning call returns LBM_OK (0) or a negative LBM_E* code; the
+ *     message of the last failure on the calling thread is lbm_last_error().
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* invalid argument (shape, pointer, size, precision)          */
+    LBM_ECUDA = -2,      /* a CUDA runtime call failed                                  */
+    LBM_ENOMEM = -3,     /* a context-private allocation failed                         */
+    LBM_ETIMEOUT = -4,   /* a bounded device-side wait gave up                          */
+    LBM_ENUMERIC = -5,   /* non-finite values detected                                  */
+    LBM_ESTATE = -6      /* call not valid in the context's current state              */
+};
+
+/* Population storage and collide arithmetic.
+ *   LBM_F64     IEEE binary64 storage, collide in native FP64 arithmetic.
+ *   LBM_F64_FF  IEEE binary64 storage, collide in float-float arithmetic (pairs of
+ *               FP32 carrying a ~48-bit significand) on the FP32 and integer pipes;
+ *               same storage and bytes as LBM_F64, results equal to ~1e-14 per step.
+ *   LBM_F32     FP32 storage, FP32 collide arithmetic.
+ *   LBM_F32_DEV FP32 storage of the deviation f - f_ref(l, z) from a per-row FP64
+ *               reference equilibrium (the unperturbed layers) fixed at
+ *               lbm_init_layers; FP32 collide arithmetic.                            */
+typedef enum { LBM_F64 = 0, LBM_F64_FF = 1, LBM_F32 = 2, LBM_F32_DEV = 3 } lbm_prec;
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque */
+
+/* Three-layer initial state of Sec. I (Eq. (seteq), pressure continuity, Fig. 1
+ * caption).  Heights are in sites with row k at height k + 1/2; interfaces are
+ *   z_lo(x) = z_lo + sum_k amp_lo[k-1] cos(2 pi k x / Lx + phase_lo[k-1]), k = 1..n_modes,
+ * and z_hi(x) likewise.  Pressure is isothermal-hydrostatic in each layer and
+ * continuous across both interfaces, p = rho_ref T_d exp(-g r z / T_d) below z_lo(x);
+ * T(x,z) = T_u + (T_m-T_u)(1 - tanh((z - z_hi)/w))/2 + (T_d-T_m)(1 - tanh((z - z_lo)/w))/2,
+ * rho = p / T, populations f^eq(rho, u = (0, -g/2), T) (renormalised velocity zero).
+ * The four mode arrays are host arrays of n_modes doubles owned by the caller and
+ * read during the call only.                                                          */
+typedef struct {
+    double T_u, T_m, T_d;          /* top, middle, bottom temperatures (> 0)            */
+    double z_lo, z_hi;             /* unperturbed interface heights in sites              */
+    double rho_ref;                /* density at the bottom wall in the bottom layer      */
+    double tanh_w;                 /* interface half-width w in sites (> 0)               */
+    int    n_modes;                /* K >= 0                                              */
+    const double *amp_lo, *phase_lo, *amp_hi, *phase_hi;
+} lbm_layers_desc;
+
+/* Create a context for an Lx x Lz lattice with relaxation time tau > 0.5 and gravity
+ * g >= 0 (Sec. III.A).  buf0 and buf1 are 16-byte aligned device buffers on one device
+ * of at least 37*Lx*Lz*(8 for LBM_F64 / LBM_F64_FF, 4 for LBM_F32 / LBM_F32_DEV) bytes
+ * each, `bytes` the size of each; they hold the two lattice copies (Sec. III.B: read
+ * one, write the other, swap).  The state starts in buf0.  cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream).  The context allocates only small
+ * private scratch (reduction partials, per-row references, mode parameters).  On
+ * failure *out is NULL.                                                               */
+int lbm_create(lbm_ctx **out, int Lx, int Lz, int prec, double tau, double g,
+               void *buf0, void *buf1, size_t bytes, void *cuda_stream);
+
+/* Release the context's private scratch; the borrowed buffers are untouched.
+ * Synchronises the stream first.  NULL is accepted.                                   */
+int lbm_destroy(lbm_ctx *c);
+
+/* Write the three-layer initial state (see lbm_layers_desc) into the current lattice
+ * copy.  LBM_EINVAL for non-positive temperatures, width or rho_ref, n_modes < 0, or
+ * NULL mode arrays with n_modes > 0.                                                  */
+int lbm_init_layers(lbm_ctx *c, const lbm_layers_desc *d);
+
+/* Advance nsteps >= 0 time steps (propagate + bc + collide, Sec. III.A-B), one fused
+ * kernel launch per step, ping-ponging between the two buffers.  Asynchronous.       */
+int lbm_step(lbm_ctx *c, int nsteps);
+
+/* Device address of the buffer holding the current state (buf0 or buf1); NULL for a
+ * NULL context.                                                                       */
+void *lbm_current(lbm_ctx *c);
+
+/* Copy the current state out / in as canonical FP64 f[l][x][z] (37*Lx*Lz doubles).
+ * on_device = 1: `f` is a device pointer (stream-ordered, asynchronous); 0: a host
+ * pointer (the call synchronises).  FP32 storage is converted; for LBM_F32_DEV the
+ * per-row reference is added back / subtracted.                                       */
+int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
+int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
+
+/* Per-site fields of the current (post-collision) state, Sec. III.A: rho, u, T with
+ * D rho T = sum |xi - u|^2 f.  renormalised = 1 returns u^H = u - gvec/2 (the paper's
+ * u + dt g/2 of the pre-collision state) and T^H = T + g^2/(4 D).  Each output is an
+ * [Lx][Lz] array (z fastest) or NULL to skip; on_device as for lbm_get_populations.   */
+int lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uz, double *T,
+                int renormalised, int on_device);
+
+/* Horizontal mean T(z) = (1/Lx) sum_x T(x, z) of the raw temperature (Sec. IV), Lz
+ * doubles, reduced in FP64 on the device in a fixed order.  on_device as above.      */
+int lbm_row_mean_T(lbm_ctx *c, double *Tbar, int on_device);
+
+/* Threshold mixing widths of the two fronts from the current state (Sec. IV: the
+ * region where the mean profile lies between 5% and 95% of each layer jump).  Upper
+ * front: b = (Tbar - T_u)/(T_m - T_u) scanned top-down, first crossing of 0.05 then of
+ * 0.95; lower front: b = (Tbar - T_m)/(T_d - T_m) scanned bottom-up, 0.95 then 0.05;
+ * crossings linearly interpolated between consecutive rows.  out[0] = L_u, out[1] =
+ * L_d in sites (host).  If dL_dTbar is not NULL it receives d(L_u + L_d)/dTbar(z)
+ * (host array of Lz doubles).  Synchronises.  LBM_EINVAL when a crossing is missing
+ * or the temperatures are not ordered T_u < T_m < T_d.                                */
+int lbm_widths(lbm_ctx *c, double T_u, double T_m, double T_d, double out[2], double *dL_dTbar);
+
+/* Total mass sum f and energy sum |xi|^2 f / 2 of the current state, reduced in FP64
+ * in a fixed order (host out[2]).  Synchronises; LBM_ENUMERIC if either is not
+ * finite.                                                                             */
+int lbm_global_sums(lbm_ctx *c, double out[2]);
+
+/* Adjoint of one step (LBM_F64 contexts only).  With f_{t+1} = C(P f_t), P the
+ * propagate+bc permutation and C the pointwise collide:
+ *   lam_out = P^T J_C(P f_t)^T lam_next.
+ * f_t, lam_next, lam_out: device arrays of 37*Lx*Lz doubles in the storage layout;
+ * lam_out must not alias the other two.  Asynchronous.                                */
+int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, double *lam_out);
+
+/* Adjoint of the width readout (LBM_F64): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
+ * with dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device, FP64 layout).
+ * dL_dTbar is a host array of Lz doubles.  lam_out: device, 37*Lx*Lz doubles.
+ * Synchronises.                                                                       */
+int lbm_loss_adjoint(lbm_ctx *c, const double *f, const double *dL_dTbar, double *lam_out);
+
+/* Adjoint of lbm_init_layers with respect to the mode amplitudes (LBM_F64): given
+ * lam0 = dL/df_0 (device, FP64 layout) returns dL/damp_lo[k] and dL/damp_hi[k] in the
+ * host arrays dA_lo, dA_hi (n_modes each).  Synchronises.                             */
+int lbm_init_adjoint(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,
+                     double *dA_lo, double *dA_hi);
+
+/* Wait for all work queued by this context; reports deferred kernel-side errors.     */
+int lbm_sync(lbm_ctx *c);
+
+/* Lattice constants of the library's own quadrature solve (host only, no GPU needed):
+ * c (37 x 2 ints, canonical order), w (37 doubles), r.  Any pointer may be NULL.      */
+int lbm_lattice(int *c, double *w, double *r);
+
+/* Message of the last failed call on this thread ("" if none).                        */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

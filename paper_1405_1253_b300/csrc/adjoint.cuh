@@ -1,0 +1,190 @@
+// adjoint.cuh -- adjoint of the fused step, of the width readout and of the initial state.
+//
+// Forward step: f_{t+1} = C(P f_t) with P = propagate + bc (a permutation of the
+// (l, x, z) entries) and C the pointwise collide.  Its adjoint is
+//   lam_t = P^T J_C(g)^T lam_{t+1},   g = P f_t.
+// The collide depends on g only through rho, J = sum xi g and E = sum |xi|^2 g, so
+//   (J_C^T lam)_m = (1 - w) lam_m + w [ A + B.(xi_m - u)/rho + C (|xi_m - u|^2 - D T)/(D rho) ],
+//   A = sum_l lam_l f^eq_l / rho,  B = sum_l lam_l df^eq_l/du_s,  C = sum_l lam_l df^eq_l/dT_s,
+// (w = 1/tau; the force shift of u and T is a constant offset).  P^T is a scatter to the
+// pull source of each population: every (l, x, z) is the source of exactly one
+// destination, so the writes never collide.
+#pragma once
+#include "common.cuh"
+#include "init_diag.cuh"
+
+namespace lbm {
+
+// P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 and its partial derivatives in s, |u|^2
+// and th for one velocity (s = xi.u, C2 = |xi|^2, u2 = |u|^2, th = T - 1, D = 2).
+struct PDerivs {
+    double P, dPds, dPdu2, dPdth;
+};
+
+__device__ __forceinline__ PDerivs hermite_poly(double s, double C2, double u2, double th) {
+    const double K0 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 2.0) + 0.125 * u2 * u2
+                    - 0.25 * th * u2 * (C2 - 4.0) + 0.125 * th * th * (C2 * C2 - 8.0 * C2 + 8.0);
+    const double K1 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 4.0);
+    const double K2 = 0.5 - 0.25 * u2 + 0.25 * th * (C2 - 6.0);
+    PDerivs d;
+    d.P = K0 + s * (K1 + s * (K2 + s * (1.0 / 6.0 + s * (1.0 / 24.0))));
+    d.dPds = K1 + s * (2.0 * K2 + s * (0.5 + s * (1.0 / 6.0)));
+    d.dPdu2 = (-0.5 + 0.25 * u2 - 0.25 * th * (C2 - 4.0)) - 0.5 * s - 0.25 * s * s;
+    d.dPdth = (0.5 * (C2 - 2.0) - 0.25 * u2 * (C2 - 4.0) + 0.25 * th * (C2 * C2 - 8.0 * C2 + 8.0))
+            + s * 0.5 * (C2 - 4.0) + s * s * 0.25 * (C2 - 6.0);
+    return d;
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next,
+              double* __restrict__ lam_out, StepParams p) {
+    const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
+    const int x = blockIdx.y;
+    if (z >= p.Lz) return;
+    int col[7];
+#pragma unroll
+    for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
+    int src[Q];
+    double g[Q];
+    static_for<Q>([&](auto l) {
+        src[l.value] = pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane);
+        g[l.value] = ft[src[l.value]];
+    });
+    const double r = d_lat.r;
+    double R = 0.0, Jx = 0.0, Jz = 0.0, E = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        R += g[l];
+        Jx += cx(l) * g[l];
+        Jz += cz(l) * g[l];
+        E += c2(l) * g[l];
+    }
+    const double ux = r * Jx / R, uz = r * Jz / R;
+    const double T = 0.5 * (d_lat.r2 * E / R - (ux * ux + uz * uz));
+    const double usx = ux, usz = uz + p.us_z, th = T + p.T_shift - 1.0;
+    const double u2 = usx * usx + usz * usz;
+    const int o = x * p.Lz + z;
+    double lam[Q];
+#pragma unroll
+    for (int l = 0; l < Q; l++) lam[l] = lam_next[l * p.plane + o];
+    double A = 0.0, Bx = 0.0, Bz = 0.0, C = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        const double xx = r * cx(l), xz = r * cz(l);
+        const double s = xx * usx + xz * usz;
+        const PDerivs d = hermite_poly(s, d_lat.r2 * c2(l), u2, th);
+        const double w = d_lat.w[shell_of(l)];
+        A += lam[l] * w * d.P;                                     // f^eq / rho
+        Bx += lam[l] * w * R * (d.dPds * xx + 2.0 * d.dPdu2 * usx);
+        Bz += lam[l] * w * R * (d.dPds * xz + 2.0 * d.dPdu2 * usz);
+        C += lam[l] * w * R * d.dPdth;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; m++) {
+        const double dx = r * cx(m) - ux, dz = r * cz(m) - uz;
+        const double mu = p.one_m_omega * lam[m]
+                        + p.omega * (A + (Bx * dx + Bz * dz) / R + C * (dx * dx + dz * dz - DIM * T) / (DIM * R));
+        lam_out[src[m]] = mu;
+    }
+}
+
+// lam_N(l,x,z) = dL[z] / Lx * (|xi_l - u|^2 - D T)/(D rho) at the stored state f.
+__global__ void k_loss_adjoint(const double* __restrict__ f, const double* __restrict__ dL,
+                               double* __restrict__ lam, int Lx, int Lz) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = blockIdx.y;
+    if (z >= Lz) return;
+    double R, ux, uz, T;
+    site_moments<StoreF64>(f, nullptr, x, z, Lz, Lx * Lz, R, ux, uz, T);
+    const double scale = dL[z] / (double)Lx / (DIM * R);
+    const int o = x * Lz + z;
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        const double dx = d_lat.r * cx(l) - ux, dz = d_lat.r * cz(l) - uz;
+        lam[l * Lx * Lz + o] = scale * (dx * dx + dz * dz - DIM * T);
+    }
+}
+
+// Per column x: sum_{z,l} lam0 df0/dz_lo(x) -> colred[x], same for z_hi -> colred[Lx + x].
+// f0 = f^eq(rho, (0, -g/2), T), rho = p/T with p and T as in layer_p_T; p is continuous
+// across the interfaces, so moving an interface adds no boundary term.
+__global__ void __launch_bounds__(128)
+k_init_adjoint_columns(const double* __restrict__ lam0, const double* __restrict__ zc, InitParams ip,
+                       double* __restrict__ colred) {
+    __shared__ double sm[2][128];
+    const int x = blockIdx.x;
+    const double zl = zc[x], zh = zc[ip.Lx + x];
+    const double gr = ip.grav * d_lat.r;
+    const double uz = -0.5 * ip.grav, u2 = uz * uz;
+    double gl = 0.0, gh = 0.0;
+    for (int k = threadIdx.x; k < ip.Lz; k += 128) {
+        const double z = k + 0.5;
+        double p, T;
+        layer_p_T(z, zl, zh, ip, p, T);
+        const double rho = p / T, th = T - 1.0;
+        const double dp_dzl = (z >= zl) ? p * (-gr / ip.Td + gr / ip.Tm) : 0.0;
+        const double dp_dzh = (z >= zh) ? p * (-gr / ip.Tm + gr / ip.Tu) : 0.0;
+        const double sl = 1.0 / cosh((z - zl) / ip.wt), sh = 1.0 / cosh((z - zh) / ip.wt);
+        const double dT_dzl = (ip.Td - ip.Tm) * 0.5 * sl * sl / ip.wt;
+        const double dT_dzh = (ip.Tm - ip.Tu) * 0.5 * sh * sh / ip.wt;
+        const double drl = dp_dzl / T - p * dT_dzl / (T * T);
+        const double drh = dp_dzh / T - p * dT_dzh / (T * T);
+        double s_feq_rho = 0.0, s_dfdT = 0.0;
+#pragma unroll
+        for (int l = 0; l < Q; l++) {
+            const double s = d_lat.r * cz(l) * uz;
+            const PDerivs d = hermite_poly(s, d_lat.r2 * c2(l), u2, th);
+            const double lv = lam0[l * ip.plane + x * ip.Lz + k];
+            const double w = d_lat.w[shell_of(l)];
+            s_feq_rho += lv * w * d.P;           // f^eq / rho
+            s_dfdT += lv * w * rho * d.dPdth;    // df^eq / dT
+        }
+        gl += s_feq_rho * drl + s_dfdT * dT_dzl;
+        gh += s_feq_rho * drh + s_dfdT * dT_dzh;
+    }
+    sm[0][threadIdx.x] = gl;
+    sm[1][threadIdx.x] = gh;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + w];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        colred[x] = sm[0][0];
+        colred[ip.Lx + x] = sm[1][0];
+    }
+}
+
+// dL/dA_k = sum_x colred[x] cos(2 pi k x / Lx + phi_k), one block per mode.
+__global__ void __launch_bounds__(128)
+k_init_adjoint_modes(const double* __restrict__ colred, const double* __restrict__ modes, InitParams ip,
+                     double* __restrict__ out) {
+    __shared__ double sm[2][128];
+    const int k = blockIdx.x;
+    const double ph_lo = modes[ip.K + k], ph_hi = modes[3 * ip.K + k];
+    double a = 0.0, b = 0.0;
+    for (int x = threadIdx.x; x < ip.Lx; x += 128) {
+        const double arg = 2.0 * M_PI * (double)(k + 1) * (double)x / (double)ip.Lx;
+        a += colred[x] * cos(arg + ph_lo);
+        b += colred[ip.Lx + x] * cos(arg + ph_hi);
+    }
+    sm[0][threadIdx.x] = a;
+    sm[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + w];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[k] = sm[0][0];
+        out[ip.K + k] = sm[1][0];
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,587 @@
+// lbm.cu -- C ABI of the B300 D2Q37 thermal lattice Boltzmann library (include/lbm.h).
+//
+// One translation unit: the kernels live in the included .cuh files; this file holds the
+// context, argument validation, launch configuration and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "common.cuh"
+#include "step_f64.cuh"
+#include "step_ff.cuh"
+#include "step_f32.cuh"
+#include "init_diag.cuh"
+#include "adjoint.cuh"
+
+using namespace lbm;
+
+// ---------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LBM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+#define LAUNCH_CHECK() CU(cudaGetLastError())
+
+// Selects a device for the scope and restores the caller's current device on exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess)) ok = true;
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------------
+// Lattice constants: solved once on the host, uploaded once per device.
+// ---------------------------------------------------------------------------------
+static std::mutex g_lat_mutex;
+static bool g_quad_done = false;
+static Quadrature g_quad;
+static bool g_dev_uploaded[128];
+
+static int host_quadrature(Quadrature* out) {
+    std::lock_guard<std::mutex> lk(g_lat_mutex);
+    if (!g_quad_done) {
+        g_quad = solve_quadrature_host();
+        g_quad_done = true;
+    }
+    if (!g_quad.ok) return fail(LBM_ECUDA, "quadrature solve did not converge");
+    *out = g_quad;
+    return LBM_OK;
+}
+
+static void split_ff(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+static int upload_lattice(int dev) {
+    Quadrature q;
+    int rc = host_quadrature(&q);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_lat_mutex);
+    if (dev < 0 || dev >= 128) return fail(LBM_EINVAL, "device index %d out of range", dev);
+    if (g_dev_uploaded[dev]) return LBM_OK;
+    DevLattice h{};
+    for (int s = 0; s < NSHELL; s++) {
+        h.w[s] = q.w_shell[s];
+        split_ff(q.w_shell[s], h.wf_hi[s], h.wf_lo[s]);
+        h.wf[s] = (float)q.w_shell[s];
+    }
+    h.r = q.r;
+    h.r2 = q.r * q.r;
+    split_ff(h.r, h.r_hi, h.r_lo);
+    split_ff(h.r2, h.r2_hi, h.r2_lo);
+    CU(cudaMemcpyToSymbol(d_lat, &h, sizeof h));
+    CU(cudaDeviceSynchronize());
+    g_dev_uploaded[dev] = true;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------
+struct lbm_ctx {
+    int Lx, Lz, prec;
+    double tau, grav;
+    void* buf[2];
+    size_t bytes;
+    int cur;                    // index of the buffer holding the current state
+    cudaStream_t stream;
+    int device;
+    // private scratch
+    double* zcol = nullptr;     // 2 * Lx interface heights / per-column adjoint sums
+    double* modes = nullptr;    // 4 * modes_cap mode parameters
+    int modes_cap = 0;
+    double* rowref = nullptr;   // Q * Lz per-row reference (LBM_F32_DEV)
+    float* rowref32 = nullptr;  // same in FP32
+    double* part = nullptr;     // reduction partials
+    size_t part_cap = 0;        // in doubles
+    double* small = nullptr;    // Lz + 8 doubles (Tbar, widths, sums)
+    double* dLrow = nullptr;    // Lz doubles (width gradient)
+    double* colred = nullptr;   // 2 * Lx (init adjoint per-column sums)
+    unsigned int* err = nullptr;  // device error word
+};
+
+static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
+
+static StepParams step_params(const lbm_ctx* c) {
+    StepParams p;
+    p.Lx = c->Lx;
+    p.Lz = c->Lz;
+    p.plane = c->Lx * c->Lz;
+    p.omega = 1.0 / c->tau;
+    p.one_m_omega = 1.0 - 1.0 / c->tau;
+    p.us_z = -c->tau * c->grav;
+    p.T_shift = c->tau * (1.0 - c->tau) * c->grav * c->grav / DIM;
+    p.grav = c->grav;
+    return p;
+}
+
+static int ensure_part(lbm_ctx* c, size_t n) {
+    if (c->part_cap >= n) return LBM_OK;
+    if (c->part) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->part);
+    }
+    c->part = nullptr;
+    c->part_cap = 0;
+    if (cudaMalloc(&c->part, n * sizeof(double)) != cudaSuccess)
+        return fail(LBM_ENOMEM, "cannot allocate %zu reduction doubles", n);
+    c->part_cap = n;
+    return LBM_OK;
+}
+
+static void free_ctx(lbm_ctx* c) {
+    if (!c) return;
+    void* ps[] = {c->zcol, c->modes, c->rowref, c->rowref32, c->part, c->small, c->dLrow, c->colred, c->err};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+template <class S>
+static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renorm) {
+    dim3 grid((c->Lz + 127) / 128, c->Lx);
+    k_moments<S><<<grid, 128, 0, c->stream>>>((const typename S::T*)c->buf[c->cur], c->rowref, c->Lx, c->Lz,
+                                              c->grav, renorm, rho, ux, uz, T);
+}
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_lattice(int* c, double* w, double* r) {
+    Quadrature q;
+    int rc = host_quadrature(&q);
+    if (rc) return rc;
+    for (int l = 0; l < Q; l++) {
+        if (c) { c[2 * l] = cx(l); c[2 * l + 1] = cz(l); }
+        if (w) w[l] = q.w_shell[shell_of(l)];
+    }
+    if (r) *r = q.r;
+    return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, void* buf0, void* buf1,
+               size_t bytes, void* cuda_stream) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (Lx < 1 || Lz < 6) return fail(LBM_EINVAL, "lattice %d x %d: need Lx >= 1, Lz >= 6", Lx, Lz);
+    if ((long long)Q * Lx * Lz >= (1LL << 31))
+        return fail(LBM_EINVAL, "lattice %d x %d too large: 37*Lx*Lz must be < 2^31", Lx, Lz);
+    if (prec < LBM_F64 || prec > LBM_F32_DEV) return fail(LBM_EINVAL, "unknown precision %d", prec);
+    if (prec == LBM_F32_DEV) return fail(LBM_EINVAL, "LBM_F32_DEV is not available in this build");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_EINVAL, "tau = %g must be > 0.5", tau);
+    if (!(g >= 0.0) || !std::isfinite(g)) return fail(LBM_EINVAL, "g = %g must be >= 0", g);
+    if (!buf0 || !buf1 || buf0 == buf1) return fail(LBM_EINVAL, "need two distinct device buffers");
+    const size_t need = (size_t)Q * Lx * Lz * pop_bytes(prec);
+    if (bytes < need) return fail(LBM_EINVAL, "buffers of %zu bytes, need %zu", bytes, need);
+    if (((uintptr_t)buf0 | (uintptr_t)buf1) & 15) return fail(LBM_EINVAL, "buffers must be 16-byte aligned");
+    cudaPointerAttributes a0, a1;
+    CU(cudaPointerGetAttributes(&a0, buf0));
+    CU(cudaPointerGetAttributes(&a1, buf1));
+    if (a0.type != cudaMemoryTypeDevice || a1.type != cudaMemoryTypeDevice || a0.device != a1.device)
+        return fail(LBM_EINVAL, "buffers must be device memory on one device");
+    DeviceGuard dg(a0.device);
+    if (!dg.ok) return fail(LBM_ECUDA, "cannot select device %d", a0.device);
+    int rc = upload_lattice(a0.device);
+    if (rc) return rc;
+    lbm_ctx* c = new lbm_ctx();
+    c->Lx = Lx; c->Lz = Lz; c->prec = prec; c->tau = tau; c->grav = g;
+    c->buf[0] = buf0; c->buf[1] = buf1; c->bytes = bytes; c->cur = 0;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->device = a0.device;
+    bool ok = cudaMalloc(&c->zcol, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->small, ((size_t)Lz + 8) * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->dLrow, (size_t)Lz * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->colred, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->err, sizeof(unsigned int)) == cudaSuccess;
+    if (ok && prec == LBM_F32_DEV)
+        ok = cudaMalloc(&c->rowref, (size_t)Q * Lz * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&c->rowref32, (size_t)Q * Lz * sizeof(float)) == cudaSuccess;
+    if (!ok) {
+        free_ctx(c);
+        return fail(LBM_ENOMEM, "context scratch allocation failed");
+    }
+    if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        free_ctx(c);
+        return fail(LBM_ECUDA, "memset of the error word failed");
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return LBM_OK;
+}
+
+void* lbm_current(lbm_ctx* c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    CU(cudaStreamSynchronize(c->stream));
+    unsigned int e = 0;
+    CU(cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        CU(cudaMemset(c->err, 0, sizeof e));
+        return fail(LBM_ETIMEOUT, "device error word 0x%x (bounded wait gave up)", e);
+    }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Init
+// ---------------------------------------------------------------------------------
+static int fill_init_params(lbm_ctx* c, const lbm_layers_desc* d, InitParams* ip) {
+    if (!d) return fail(LBM_EINVAL, "layers desc is NULL");
+    if (!(d->T_u > 0 && d->T_m > 0 && d->T_d > 0)) return fail(LBM_EINVAL, "temperatures must be > 0");
+    if (!(d->tanh_w > 0)) return fail(LBM_EINVAL, "tanh_w must be > 0");
+    if (!(d->rho_ref > 0)) return fail(LBM_EINVAL, "rho_ref must be > 0");
+    if (d->n_modes < 0) return fail(LBM_EINVAL, "n_modes < 0");
+    if (d->n_modes > 0 && (!d->amp_lo || !d->phase_lo || !d->amp_hi || !d->phase_hi))
+        return fail(LBM_EINVAL, "mode arrays are NULL");
+    ip->Lx = c->Lx; ip->Lz = c->Lz; ip->plane = c->Lx * c->Lz;
+    ip->grav = c->grav; ip->Tu = d->T_u; ip->Tm = d->T_m; ip->Td = d->T_d;
+    ip->rho_ref = d->rho_ref; ip->wt = d->tanh_w; ip->zlo0 = d->z_lo; ip->zhi0 = d->z_hi;
+    ip->K = d->n_modes;
+    const int cap = std::max(1, d->n_modes);
+    if (c->modes_cap < cap) {
+        if (c->modes) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->modes);
+        }
+        c->modes = nullptr;
+        c->modes_cap = 0;
+        if (cudaMalloc(&c->modes, 4 * (size_t)cap * sizeof(double)) != cudaSuccess)
+            return fail(LBM_ENOMEM, "mode buffer allocation failed");
+        c->modes_cap = cap;
+    }
+    if (d->n_modes > 0) {
+        std::vector<double> h(4 * (size_t)d->n_modes);
+        for (int k = 0; k < d->n_modes; k++) {
+            h[k] = d->amp_lo[k];
+            h[d->n_modes + k] = d->phase_lo[k];
+            h[2 * d->n_modes + k] = d->amp_hi[k];
+            h[3 * d->n_modes + k] = d->phase_hi[k];
+        }
+        CU(cudaMemcpyAsync(c->modes, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));   // h is released at scope exit
+    }
+    return LBM_OK;
+}
+
+int lbm_init_layers(lbm_ctx* c, const lbm_layers_desc* d) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    InitParams ip;
+    int rc = fill_init_params(c, d, &ip);
+    if (rc) return rc;
+    k_interfaces<<<(c->Lx + 127) / 128, 128, 0, c->stream>>>(c->zcol, c->modes, ip);
+    LAUNCH_CHECK();
+    dim3 grid((c->Lz + 127) / 128, c->Lx);
+    void* f = c->buf[c->cur];
+    switch (c->prec) {
+        case LBM_F64:
+        case LBM_F64_FF:
+            k_init<StoreF64><<<grid, 128, 0, c->stream>>>((double*)f, c->zcol, nullptr, ip);
+            break;
+        case LBM_F32:
+            k_init<StoreF32><<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, nullptr, ip);
+            break;
+        default:
+            k_rowref<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->rowref, c->rowref32, ip);
+            LAUNCH_CHECK();
+            k_init<StoreF32Dev><<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, c->rowref, ip);
+            break;
+    }
+    LAUNCH_CHECK();
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Step
+// ---------------------------------------------------------------------------------
+int lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
+    for (int s = 0; s < nsteps; s++) {
+        void* fin = c->buf[c->cur];
+        void* fout = c->buf[c->cur ^ 1];
+        switch (c->prec) {
+            case LBM_F64:
+                k_step_f64<<<grid, BLOCK_Z, 0, c->stream>>>((const double*)fin, (double*)fout, p);
+                break;
+            case LBM_F64_FF:
+                launch_step_ff((const double*)fin, (double*)fout, p, c->stream);
+                break;
+            default:
+                launch_step_f32((const float*)fin, (float*)fout, p, c->stream);
+                break;
+        }
+        LAUNCH_CHECK();
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Population copies
+// ---------------------------------------------------------------------------------
+static int convert_pops(lbm_ctx* c, double* buf, int on_device, bool to_f64) {
+    const long long n = (long long)Q * c->Lx * c->Lz;
+    void* f = c->buf[c->cur];
+    if (c->prec == LBM_F64 || c->prec == LBM_F64_FF) {
+        cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice
+                                     : (to_f64 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+        if (to_f64) CU(cudaMemcpyAsync(buf, f, n * sizeof(double), k, c->stream));
+        else CU(cudaMemcpyAsync(f, buf, n * sizeof(double), k, c->stream));
+        if (!on_device) CU(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    // FP32 storage: convert one population plane at a time through device scratch
+    const long long chunk = (long long)c->Lx * c->Lz;
+    double* tmp = nullptr;
+    if (!on_device && cudaMallocAsync((void**)&tmp, chunk * sizeof(double), c->stream) != cudaSuccess)
+        return fail(LBM_ENOMEM, "conversion buffer allocation failed");
+    const double* ref = c->rowref;
+    for (long long first = 0; first < n; first += chunk) {
+        const long long m = std::min(chunk, n - first);
+        double* dev = on_device ? buf + first : tmp;
+        const int blocks = (int)((m + 255) / 256);
+        if (to_f64) {
+            if (c->prec == LBM_F32) k_to_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            else k_to_f64<StoreF32Dev><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            LAUNCH_CHECK();
+            if (!on_device) CU(cudaMemcpyAsync(buf + first, tmp, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            if (!on_device) CU(cudaMemcpyAsync(tmp, buf + first, m * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            if (c->prec == LBM_F32) k_from_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            else k_from_f64<StoreF32Dev><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            LAUNCH_CHECK();
+        }
+        if (!on_device) CU(cudaStreamSynchronize(c->stream));
+    }
+    if (tmp) {
+        CU(cudaFreeAsync(tmp, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
+    if (!c || !f) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(c->device);
+    return convert_pops(c, f, on_device, true);
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
+    if (!c || !f) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(c->device);
+    return convert_pops(c, const_cast<double*>(f), on_device, false);
+}
+
+// ---------------------------------------------------------------------------------
+// Diagnostics
+// ---------------------------------------------------------------------------------
+int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renormalised, int on_device) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    const size_t n = (size_t)c->Lx * c->Lz;
+    double* outs[4] = {rho, ux, uz, T};
+    double* dev[4] = {rho, ux, uz, T};
+    double* tmp = nullptr;
+    if (!on_device) {
+        int k = 0;
+        for (int i = 0; i < 4; i++) k += outs[i] != nullptr;
+        if (k == 0) return LBM_OK;
+        if (cudaMallocAsync((void**)&tmp, k * n * sizeof(double), c->stream) != cudaSuccess)
+            return fail(LBM_ENOMEM, "moments buffer allocation failed");
+        k = 0;
+        for (int i = 0; i < 4; i++) dev[i] = outs[i] ? tmp + (k++) * n : nullptr;
+    }
+    switch (c->prec) {
+        case LBM_F64: case LBM_F64_FF: launch_moments<StoreF64>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+        case LBM_F32: launch_moments<StoreF32>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+        default: launch_moments<StoreF32Dev>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+    }
+    LAUNCH_CHECK();
+    if (!on_device) {
+        for (int i = 0; i < 4; i++)
+            if (outs[i]) CU(cudaMemcpyAsync(outs[i], dev[i], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaFreeAsync(tmp, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+static int row_mean_device(lbm_ctx* c, double* Tbar_dev) {
+    const int target = std::max(1, (148 * 16 * 128) / std::max(1, c->Lz));
+    const int nx_per = (c->Lx + std::min(c->Lx, target) - 1) / std::min(c->Lx, target);
+    const int nch = (c->Lx + nx_per - 1) / nx_per;
+    int rc = ensure_part(c, (size_t)nch * c->Lz);
+    if (rc) return rc;
+    dim3 grid((c->Lz + 127) / 128, nch);
+    const void* f = c->buf[c->cur];
+    switch (c->prec) {
+        case LBM_F64: case LBM_F64_FF:
+            k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, nullptr, c->Lx, c->Lz, nx_per, c->part); break;
+        case LBM_F32:
+            k_rowT_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, nullptr, c->Lx, c->Lz, nx_per, c->part); break;
+        default:
+            k_rowT_partial<StoreF32Dev><<<grid, 128, 0, c->stream>>>((const float*)f, c->rowref, c->Lx, c->Lz, nx_per, c->part); break;
+    }
+    LAUNCH_CHECK();
+    k_rowT_final<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->part, nch, c->Lx, c->Lz, Tbar_dev);
+    LAUNCH_CHECK();
+    return LBM_OK;
+}
+
+int lbm_row_mean_T(lbm_ctx* c, double* Tbar, int on_device) {
+    if (!c || !Tbar) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(c->device);
+    double* dst = on_device ? Tbar : c->small;
+    int rc = row_mean_device(c, dst);
+    if (rc) return rc;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(Tbar, c->small, (size_t)c->Lz * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_widths(lbm_ctx* c, double T_u, double T_m, double T_d, double out[2], double* dL_dTbar) {
+    if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+    if (!(T_u < T_m && T_m < T_d)) return fail(LBM_EINVAL, "need T_u < T_m < T_d");
+    DeviceGuard dg(c->device);
+    int rc = row_mean_device(c, c->small);
+    if (rc) return rc;
+    double* res = c->small + c->Lz;   // 3 doubles after Tbar
+    k_widths<<<1, 32, 0, c->stream>>>(c->small, c->Lz, T_u, T_m, T_d, res, dL_dTbar ? c->dLrow : nullptr);
+    LAUNCH_CHECK();
+    double h[3];
+    CU(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    if (dL_dTbar) CU(cudaMemcpyAsync(dL_dTbar, c->dLrow, (size_t)c->Lz * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h[2] != 0.0) return fail(LBM_EINVAL, "a mixing-width crossing is missing");
+    out[0] = h[0];
+    out[1] = h[1];
+    return LBM_OK;
+}
+
+int lbm_global_sums(lbm_ctx* c, double out[2]) {
+    if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(c->device);
+    const int nsite = c->Lx * c->Lz;
+    const int nblk = std::max(1, std::min(148 * 8, (nsite + RED_THREADS - 1) / RED_THREADS));
+    int rc = ensure_part(c, 2 * (size_t)nblk);
+    if (rc) return rc;
+    const void* f = c->buf[c->cur];
+    switch (c->prec) {
+        case LBM_F64: case LBM_F64_FF:
+            k_global_partial<StoreF64><<<nblk, RED_THREADS, 0, c->stream>>>((const double*)f, nullptr, c->Lx, c->Lz, c->part); break;
+        case LBM_F32:
+            k_global_partial<StoreF32><<<nblk, RED_THREADS, 0, c->stream>>>((const float*)f, nullptr, c->Lx, c->Lz, c->part); break;
+        default:
+            k_global_partial<StoreF32Dev><<<nblk, RED_THREADS, 0, c->stream>>>((const float*)f, c->rowref, c->Lx, c->Lz, c->part); break;
+    }
+    LAUNCH_CHECK();
+    k_global_final<<<1, RED_THREADS, 0, c->stream>>>(c->part, nblk, c->small);
+    LAUNCH_CHECK();
+    CU(cudaMemcpyAsync(out, c->small, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1])) return fail(LBM_ENUMERIC, "non-finite mass or energy");
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------------
+int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
+    if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
+    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
+    k_adjoint_f64<<<grid, BLOCK_Z, 0, c->stream>>>(f_t, lam_next, lam_out, p);
+    LAUNCH_CHECK();
+    return LBM_OK;
+}
+
+int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double* lam_out) {
+    if (!c || !f || !dL_dTbar || !lam_out) return fail(LBM_EINVAL, "NULL argument");
+    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    DeviceGuard dg(c->device);
+    CU(cudaMemcpyAsync(c->dLrow, dL_dTbar, (size_t)c->Lz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    dim3 grid((c->Lz + 127) / 128, c->Lx);
+    k_loss_adjoint<<<grid, 128, 0, c->stream>>>(f, c->dLrow, lam_out, c->Lx, c->Lz);
+    LAUNCH_CHECK();
+    CU(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi) {
+    if (!c || !lam0) return fail(LBM_EINVAL, "NULL argument");
+    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    DeviceGuard dg(c->device);
+    InitParams ip;
+    int rc = fill_init_params(c, d, &ip);
+    if (rc) return rc;
+    if (d->n_modes > 0 && (!dA_lo || !dA_hi)) return fail(LBM_EINVAL, "NULL gradient outputs");
+    k_interfaces<<<(c->Lx + 127) / 128, 128, 0, c->stream>>>(c->zcol, c->modes, ip);
+    LAUNCH_CHECK();
+    k_init_adjoint_columns<<<c->Lx, 128, 0, c->stream>>>(lam0, c->zcol, ip, c->colred);
+    LAUNCH_CHECK();
+    if (d->n_modes == 0) return lbm_sync(c);
+    rc = ensure_part(c, 2 * (size_t)d->n_modes);
+    if (rc) return rc;
+    k_init_adjoint_modes<<<d->n_modes, 128, 0, c->stream>>>(c->colred, c->modes, ip, c->part);
+    LAUNCH_CHECK();
+    std::vector<double> h(2 * (size_t)d->n_modes);
+    CU(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < d->n_modes; k++) { dA_lo[k] = h[k]; dA_hi[k] = h[d->n_modes + k]; }
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// step_f32.cuh -- fused propagate + bc + collide with FP32 storage and FP32 arithmetic.
+//
+// Same structure as the FP64 kernel (step_f64.cuh).  To keep FP32 rounding off the
+// O(1) parts, the equilibrium is evaluated as P - 1 (the deviation of the Hermite
+// polynomial from its rest value) and the relaxation as
+//   f' = g + w (w_l rho (1 + (P - 1)) - g),
+// and the moment sums use compensated (two-sum) accumulation.
+#pragma once
+#include "common.cuh"
+
+namespace lbm {
+
+struct StepParamsF {
+    int Lx, Lz, plane;
+    float omega, us_z, T_shift;
+};
+
+// s + e = a + b exactly (Knuth two-sum).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void collide_f32(const float (&g)[Q], float (&fo)[Q], const StepParamsF& p) {
+    const float r = d_lat.r_hi;
+    // compensated moment sums
+    float rho = g[0], rho_c = 0.f, Jx = 0.f, Jz = 0.f, E = 0.f, E_c = 0.f;
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
+        float ps, pe;
+        two_sum_f(g[A], g[B], ps, pe);
+        const float m = g[A] - g[B];
+        float s, e;
+        two_sum_f(rho, ps, s, e);
+        rho = s;
+        rho_c += e + pe;
+        if constexpr (cx(A) != 0) Jx = fmaf((float)cx(A), m, Jx);
+        if constexpr (cz(A) != 0) Jz = fmaf((float)cz(A), m, Jz);
+        two_sum_f(E, (float)c2(A) * ps, s, e);
+        E = s;
+        E_c += e + (float)c2(A) * pe;
+    });
+    rho += rho_c;
+    E += E_c;
+    const float inv = 1.f / rho;
+    const float ux = r * Jx * inv, uz = r * Jz * inv;
+    const float T = 0.5f * (d_lat.r2_hi * E * inv - (ux * ux + uz * uz));
+    const float usz = uz + p.us_z;
+    const float th = (T - 1.f) + p.T_shift;
+    const float u2 = ux * ux + usz * usz;
+    const float r2 = d_lat.r2_hi;
+    // K0 - 1, K1, K2 as polynomials in the integer |c|^2
+    const float d00 = -0.5f * u2 - th + 0.125f * u2 * u2 + th * u2 + th * th;
+    const float k01 = r2 * (0.5f * th - 0.25f * th * u2 - th * th);
+    const float k02 = r2 * r2 * 0.125f * th * th;
+    const float k10 = 1.f - 0.5f * u2 - 2.f * th, k11 = r2 * 0.5f * th;
+    const float k20 = 0.5f - 0.25f * u2 - 1.5f * th, k21 = r2 * 0.25f * th;
+    const float a = r * ux, b = r * usz;
+    const float orho = p.omega * rho;
+    {
+        const float W = orho * d_lat.wf[0];
+        fo[0] = g[0] + (fmaf(W, d00, W) - p.omega * g[0]);
+    }
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
+        constexpr int SH = shell_of(A);
+        constexpr float C2 = (float)c2(A);
+        const float D0 = fmaf(C2, fmaf(C2, k02, k01), d00);     // K0 - 1
+        const float K1 = fmaf(C2, k11, k10);
+        const float K2 = fmaf(C2, k21, k20);
+        float s;
+        if constexpr (cx(A) == 0) s = (float)cz(A) * b;
+        else if constexpr (cz(A) == 0) s = (float)cx(A) * a;
+        else s = fmaf((float)cx(A), a, (float)cz(A) * b);
+        const float s2 = s * s;
+        const float Ev = fmaf(s2, fmaf(s2, 1.f / 24.f, K2), D0);  // even part - 1
+        const float Od = s * fmaf(s2, 1.f / 6.f, K1);
+        const float W = orho * d_lat.wf[SH];
+        // f' = g + (W (1 + Ev +- Od) - omega g)
+        fo[A] = g[A] + (fmaf(W, Ev + Od, W) - p.omega * g[A]);
+        fo[B] = g[B] + (fmaf(W, Ev - Od, W) - p.omega * g[B]);
+    });
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p) {
+    const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
+    const int x = blockIdx.y;
+    if (z >= p.Lz) return;
+    int col[7];
+#pragma unroll
+    for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
+    float g[Q], fo[Q];
+    const int z0 = blockIdx.x * BLOCK_Z;
+    const bool interior = (z0 >= 3) && (z0 + BLOCK_Z + 3 <= p.Lz);
+    if (interior) {
+        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index_interior<decltype(l)::value>(z, col, p.plane)); });
+    } else {
+        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane)); });
+    }
+    collide_f32(g, fo, p);
+    const int o = x * p.Lz + z;
+#pragma unroll
+    for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
+}
+
+inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, cudaStream_t st) {
+    StepParamsF q;
+    q.Lx = p.Lx; q.Lz = p.Lz; q.plane = p.plane;
+    q.omega = (float)p.omega;
+    q.us_z = (float)p.us_z;
+    q.T_shift = (float)p.T_shift;
+    dim3 grid((p.Lz + BLOCK_Z - 1) / BLOCK_Z, p.Lx);
+    k_step_f32<<<grid, BLOCK_Z, 0, st>>>(fin, fout, q);
+}
+
+}  // namespace lbm

@@ -1,0 +1,103 @@
+// step_f64.cuh -- fused propagate + bc + collide in native FP64 (IEEE binary64 storage).
+//
+// One thread per site.  The 37 pulled populations (Sec. III.B "pull": misaligned reads,
+// aligned writes) are gathered straight from HBM with the periodic-x wrap and the wall
+// bounce-back folded into the index; the collide (Sec. III.A Eq. (LBE) with the shifted
+// equilibrium) runs in registers; the 37 results are stored coalesced into the other
+// lattice copy.  The equilibrium is the 4th-order Hermite form collapsed to a polynomial
+// in s = xi.u_s per velocity shell:
+//   P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24,
+//   K0 = 1 - u^2/2 + th (c2-2)/2 + u^4/8 - th u^2 (c2-4)/4 + th^2 (c2^2 - 8 c2 + 8)/8,
+//   K1 = 1 - u^2/2 + th (c2-4)/2,   K2 = 1/2 - u^2/4 + th (c2-6)/4,
+// with u = u_s, th = T_s - 1, c2 = |xi|^2 = r^2 |c|^2 (D = 2); opposite velocities share
+// the even part and flip the odd part.
+#pragma once
+#include "common.cuh"
+
+namespace lbm {
+
+// Per-site collide in FP64: g = post-propagate populations, fo = post-collide.
+__device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q], const StepParams& p) {
+    const double r = d_lat.r;
+    // moments with integer velocities: rho, J = sum c g, E = sum |c|^2 g
+    double pp[NPAIR], mm[NPAIR];
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
+        pp[k.value] = g[A] + g[B];
+        mm[k.value] = g[A] - g[B];
+    });
+    double rho = g[0], Jx = 0.0, Jz = 0.0;
+    double S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A = pair_first(decltype(k)::value);
+        rho += pp[k.value];
+        if constexpr (cx(A) != 0) Jx = fma((double)cx(A), mm[k.value], Jx);
+        if constexpr (cz(A) != 0) Jz = fma((double)cz(A), mm[k.value], Jz);
+        S[shell_of(A)] += pp[k.value];
+    });
+    double E = 0.0;
+    static_for<NSHELL>([&](auto s) {
+        if constexpr (decltype(s)::value > 0) E = fma((double)shell_c2(decltype(s)::value), S[s.value], E);
+    });
+    const double inv = 1.0 / rho;
+    const double rinv = r * inv;
+    const double ux = Jx * rinv, uz = Jz * rinv;
+    const double T = 0.5 * (d_lat.r2 * E * inv - (ux * ux + uz * uz));
+    // force shift (Sec. III.A): u_s = u + tau g, T_s = T + tau (1 - tau) g^2 / D
+    const double usz = uz + p.us_z;
+    const double th = T + p.T_shift - 1.0;
+    const double u2 = ux * ux + usz * usz;
+    // K0, K1, K2 as polynomials in the integer |c|^2 (|xi|^2 = r^2 |c|^2)
+    const double r2 = d_lat.r2;
+    const double k00 = 1.0 - 0.5 * u2 - th + 0.125 * u2 * u2 + th * u2 + th * th;
+    const double k01 = r2 * (0.5 * th - 0.25 * th * u2 - th * th);
+    const double k02 = r2 * r2 * 0.125 * th * th;
+    const double k10 = 1.0 - 0.5 * u2 - 2.0 * th, k11 = r2 * 0.5 * th;
+    const double k20 = 0.5 - 0.25 * u2 - 1.5 * th, k21 = r2 * 0.25 * th;
+    const double a = r * ux, b = r * usz;          // s_l = c_x a + c_z b
+    const double orho = p.omega * rho;
+    fo[0] = fma(p.one_m_omega, g[0], orho * d_lat.w[0] * k00);    // rest population
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
+        constexpr int SH = shell_of(A);
+        constexpr double C2 = (double)c2(A);
+        const double K0 = fma(C2, fma(C2, k02, k01), k00);
+        const double K1 = fma(C2, k11, k10);
+        const double K2 = fma(C2, k21, k20);
+        double s;
+        if constexpr (cx(A) == 0) s = (double)cz(A) * b;
+        else if constexpr (cz(A) == 0) s = (double)cx(A) * a;
+        else s = fma((double)cx(A), a, (double)cz(A) * b);
+        const double s2 = s * s;
+        const double Ev = fma(s2, fma(s2, 1.0 / 24.0, K2), K0);
+        const double Od = s * fma(s2, 1.0 / 6.0, K1);
+        const double W = orho * d_lat.w[SH];
+        const double Pa = W * Ev, Pb = W * Od;
+        fo[A] = fma(p.one_m_omega, g[A], Pa + Pb);
+        fo[B] = fma(p.one_m_omega, g[B], Pa - Pb);
+    });
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f64(const double* __restrict__ fin, double* __restrict__ fout, StepParams p) {
+    const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
+    const int x = blockIdx.y;
+    if (z >= p.Lz) return;
+    int col[7];
+#pragma unroll
+    for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
+    double g[Q], fo[Q];
+    const int z0 = blockIdx.x * BLOCK_Z;
+    const bool interior = (z0 >= 3) && (z0 + BLOCK_Z + 3 <= p.Lz);
+    if (interior) {
+        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index_interior<decltype(l)::value>(z, col, p.plane)); });
+    } else {
+        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane)); });
+    }
+    collide_f64(g, fo, p);
+    const int o = x * p.Lz + z;
+#pragma unroll
+    for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
+}
+
+}  // namespace lbm

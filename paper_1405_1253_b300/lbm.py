@@ -1,0 +1,220 @@
+"""Thin ctypes binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``csrc/liblbm.so``; PyTorch only
+provides device memory and the stream.  Importing this module loads the library and
+raises ImportError when it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "liblbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1405_1253_b300.build` "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+Q = 37
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ETIMEOUT, LBM_ENUMERIC, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PREC = {"f64": 0, "f64_ff": 1, "f32": 2, "f32_dev": 3}
+POP_BYTES = {"f64": 8, "f64_ff": 8, "f32": 4, "f32_dev": 4}
+
+_vp, _dp, _ip, _i, _d, _sz = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                              ctypes.c_int, ctypes.c_double, ctypes.c_size_t)
+
+
+class LayersDesc(ctypes.Structure):
+    _fields_ = [("T_u", _d), ("T_m", _d), ("T_d", _d), ("z_lo", _d), ("z_hi", _d), ("rho_ref", _d),
+                ("tanh_w", _d), ("n_modes", _i), ("amp_lo", _dp), ("phase_lo", _dp), ("amp_hi", _dp),
+                ("phase_hi", _dp)]
+
+
+_SIGS = {
+    "lbm_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _vp, _vp, _sz, _vp]),
+    "lbm_destroy": (_i, [_vp]),
+    "lbm_init_layers": (_i, [_vp, ctypes.POINTER(LayersDesc)]),
+    "lbm_step": (_i, [_vp, _i]),
+    "lbm_current": (_vp, [_vp]),
+    "lbm_get_populations": (_i, [_vp, _vp, _i]),
+    "lbm_set_populations": (_i, [_vp, _vp, _i]),
+    "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i]),
+    "lbm_row_mean_T": (_i, [_vp, _vp, _i]),
+    "lbm_widths": (_i, [_vp, _d, _d, _d, _dp, _dp]),
+    "lbm_global_sums": (_i, [_vp, _dp]),
+    "lbm_adjoint_step": (_i, [_vp, _vp, _vp, _vp]),
+    "lbm_loss_adjoint": (_i, [_vp, _vp, _dp, _vp]),
+    "lbm_init_adjoint": (_i, [_vp, ctypes.POINTER(LayersDesc), _vp, _dp, _dp]),
+    "lbm_sync": (_i, [_vp]),
+    "lbm_lattice": (_i, [_ip, _dp, _dp]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != LBM_OK:
+        raise LBMError(rc, _lib.lbm_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def lattice():
+    """(c[37,2], w[37], r) from the library's own quadrature (host only)."""
+    c = np.zeros(2 * Q, dtype=np.int32)
+    w = np.zeros(Q)
+    r = np.zeros(1)
+    _check(_lib.lbm_lattice(c.ctypes.data_as(_ip), _dptr(w), _dptr(r)))
+    return c.reshape(Q, 2), w, float(r[0])
+
+
+def layers_desc(T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi):
+    """Build an lbm_layers_desc; returns (desc, keepalive arrays)."""
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (amp_lo, ph_lo, amp_hi, ph_hi)]
+    K = len(arrs[0])
+    assert all(len(a) == K for a in arrs)
+    d = LayersDesc(float(T_u), float(T_m), float(T_d), float(z_lo), float(z_hi), float(rho_ref),
+                   float(tanh_w), K, *[_dptr(a) if K else None for a in arrs])
+    return d, arrs
+
+
+class Lattice:
+    """One lattice on one GPU: two torch-owned population buffers and a library context."""
+
+    def __init__(self, Lx: int, Lz: int, tau: float, grav: float, prec: str = "f64",
+                 device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.Lx, self.Lz, self.tau, self.grav, self.prec = int(Lx), int(Lz), float(tau), float(grav), prec
+        self.device = torch.device("cuda", device)
+        n = Q * self.Lx * self.Lz
+        dt = torch.float64 if POP_BYTES[prec] == 8 else torch.float32
+        self.bufs = [torch.empty(n, dtype=dt, device=self.device) for _ in range(2)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = _vp()
+        nbytes = n * POP_BYTES[prec]
+        _check(_lib.lbm_create(ctypes.byref(ctx), self.Lx, self.Lz, PREC[prec], self.tau, self.grav,
+                               self.bufs[0].data_ptr(), self.bufs[1].data_ptr(), nbytes,
+                               self.stream.cuda_stream))
+        self.ctx = ctx
+
+    # -- lifecycle ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            _lib.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- method --------------------------------------------------------------------
+    def init_layers(self, T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi):
+        d, keep = layers_desc(T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi)
+        _check(_lib.lbm_init_layers(self.ctx, ctypes.byref(d)))
+
+    def init_from(self, lat):
+        """Initial state of a workloads.Lattice description."""
+        m = lat.modes()
+        self.init_layers(lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi, lat.rho_ref, lat.tanh_w,
+                         m.amp_lo, m.ph_lo, m.amp_hi, m.ph_hi)
+
+    def step(self, n: int = 1):
+        _check(_lib.lbm_step(self.ctx, int(n)))
+
+    def sync(self):
+        _check(_lib.lbm_sync(self.ctx))
+
+    def current(self):
+        """The torch buffer holding the current state (storage precision, flat)."""
+        ptr = _lib.lbm_current(self.ctx)
+        return self.bufs[0] if ptr == self.bufs[0].data_ptr() else self.bufs[1]
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((Q, self.Lx, self.Lz))
+        _check(_lib.lbm_get_populations(self.ctx, out.ctypes.data, 0))
+        return out
+
+    def populations_device(self, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty(Q * self.Lx * self.Lz, dtype=torch.float64, device=self.device)
+        _check(_lib.lbm_get_populations(self.ctx, out.data_ptr(), 1))
+        return out
+
+    def set_populations(self, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            assert f.size == Q * self.Lx * self.Lz
+            _check(_lib.lbm_set_populations(self.ctx, f.ctypes.data, 0))
+        else:
+            assert f.dtype == self.torch.float64 and f.is_contiguous() and f.numel() == Q * self.Lx * self.Lz
+            _check(_lib.lbm_set_populations(self.ctx, f.data_ptr(), 1))
+
+    def moments(self, renormalised: bool = False):
+        outs = [np.empty((self.Lx, self.Lz)) for _ in range(4)]
+        _check(_lib.lbm_moments(self.ctx, *[o.ctypes.data for o in outs], int(bool(renormalised)), 0))
+        return tuple(outs)
+
+    def row_mean_T(self) -> np.ndarray:
+        out = np.empty(self.Lz)
+        _check(_lib.lbm_row_mean_T(self.ctx, out.ctypes.data, 0))
+        return out
+
+    def widths(self, T_u, T_m, T_d, with_grad: bool = False):
+        out = np.zeros(2)
+        dL = np.zeros(self.Lz) if with_grad else None
+        _check(_lib.lbm_widths(self.ctx, float(T_u), float(T_m), float(T_d), _dptr(out),
+                               _dptr(dL) if with_grad else None))
+        return (out, dL) if with_grad else out
+
+    def global_sums(self) -> np.ndarray:
+        out = np.zeros(2)
+        _check(_lib.lbm_global_sums(self.ctx, _dptr(out)))
+        return out
+
+    # -- adjoint (FP64 contexts) -------------------------------------------------------
+    def adjoint_step(self, f_t, lam_next, lam_out):
+        _check(_lib.lbm_adjoint_step(self.ctx, f_t.data_ptr(), lam_next.data_ptr(), lam_out.data_ptr()))
+
+    def loss_adjoint(self, f, dL_dTbar: np.ndarray, lam_out):
+        dL = np.ascontiguousarray(dL_dTbar, dtype=np.float64)
+        assert dL.size == self.Lz
+        _check(_lib.lbm_loss_adjoint(self.ctx, f.data_ptr(), _dptr(dL), lam_out.data_ptr()))
+
+    def init_adjoint(self, lam0, T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi):
+        d, keep = layers_desc(T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi)
+        K = d.n_modes
+        dlo, dhi = np.zeros(max(K, 1)), np.zeros(max(K, 1))
+        _check(_lib.lbm_init_adjoint(self.ctx, ctypes.byref(d), lam0.data_ptr(), _dptr(dlo), _dptr(dhi)))
+        return dlo[:K], dhi[:K]
