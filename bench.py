@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the D2Q37 thermal lattice Boltzmann step on B300.
+
+One benchmark step = one fused propagate + bc + collide launch (lbm_step(1)) over the
+whole 1024 x 2048 three-layer Rayleigh-Taylor lattice (tau = 0.7, g = 5e-5, 64 seeded
+interface modes of amplitude std 0.5).  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f64_ff|f64|f32] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank advances its own independent replica
+(weak scaling; the lattices do not exchange data) and rank 0 reports the aggregate.
+--impl reference times the plain FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1405_1253_b300 import workloads as W  # noqa: E402
+
+Q = 37
+METRIC = "MLUPS and % HBM roofline, FP64 vs FP32-storage (stated error), adjoint/forward"
+BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4}
+ARITH = {"f64": "f64", "f64_ff": "f32x2", "f32": "f32"}
+KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1405_1253_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, sites: int):
+    """Per-launch DRAM bytes from profiles/, if taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = csrc_hash()
+    for line in open(path):
+        m = re.match(r"TRAFFIC kernel=(\S+) src=(\S+) bytes_per_site=([0-9.eE+-]+)", line.strip())
+        if m and m.group(1) == kernel and m.group(2) == want:
+            return float(m.group(3)) * sites
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cores_used() -> int:
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    if os.environ.get("OMP_NUM_THREADS"):
+        n = min(n, int(os.environ["OMP_NUM_THREADS"]))
+    return n
+
+
+def time_oracle(lat, ncols: int, nsteps: int):
+    """Oracle MLUPS on an ncols-column window of the lattice (periodic in the window)."""
+    import oracle
+    a = lat.layer_args()
+    f = oracle.init_layers(lat.Lx, lat.Lz, **a)
+    win = np.ascontiguousarray(f[:, :ncols, :])
+    t0 = time.perf_counter()
+    oracle.step(win, lat.tau, lat.grav, nsteps)
+    dt = time.perf_counter() - t0
+    return ncols * lat.Lz * nsteps / dt / 1e6, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    lat = W.THROUGHPUT_1024x2048
+    ncols = 256
+    for _ in range(args.warmup):
+        time_oracle(lat, ncols, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = time_oracle(lat, ncols, 1)
+        times.append(dt)
+    tot = sum(times)
+    mlups = ncols * lat.Lz * args.steps / tot / 1e6
+    sample = f"{ncols}x{lat.Lz} column window of the {lat.Lx}x{lat.Lz} workload, 1 oracle step per timed step"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded three-layer Rayleigh-Taylor initial state)",
+            "config": {"workload": "three-layer RT, D2Q37, 1024x2048, tau=0.7, g=5e-5, 64 modes",
+                       "Lx": lat.Lx, "Lz": lat.Lz, "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_variant(torch, lbm, lat, prec, steps, warmup, stream):
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+    L.init_from(lat)
+    L.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    L.close()
+    return ms
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1405_1253_b300 import lbm
+    lat = W.THROUGHPUT_1024x2048
+    sites = lat.sites
+    prec = args.prec
+    stream = torch.cuda.current_stream()
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+    L.init_from(lat)
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    mlups = ws * sites / (ms_step * 1e-3) / 1e6
+    mass = L.global_sums()[0]
+
+    # end to end through the C ABI with host buffers: host -> device state, one step,
+    # device -> host state, every step (pinned host memory)
+    n = Q * sites
+    h_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h_in.copy_(L.populations_device().cpu())
+    e2e_steps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lbm._check(lbm._lib.lbm_set_populations(L.ctx, h_in.data_ptr(), 0))
+        L.step(1)
+        lbm._check(lbm._lib.lbm_get_populations(L.ctx, h_out.data_ptr(), 0))
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_mlups = ws * sites / e2e_s / 1e6
+    L.close()
+
+    variants = {}
+    if not args.no_variants:
+        for v in ("f64_ff", "f64", "f32"):
+            vsteps = 10 if v == "f64" else 20
+            vms = time_variant(torch, lbm, lat, v, vsteps, 3, stream)
+            vbytes = 2 * Q * BYTES_PER_POP[v] * sites
+            variants[v] = {"mlups": sites / (vms * 1e-3) / 1e6, "ms_per_step": vms,
+                           "gbs": vbytes / (vms * 1e-3) / 1e9, "arith": ARITH[v]}
+
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    alg_bytes = 2 * Q * BYTES_PER_POP[prec] * sites
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    for v in variants.values():
+        v["hbm_frac"] = v["gbs"] / peak
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        ncols = 128
+        cpu_mlups, cpu_s = time_oracle(lat, ncols, 3)
+        cpu = {"value": cpu_mlups, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+               "sample": f"{ncols}x{lat.Lz} column window of the {lat.Lx}x{lat.Lz} workload, 3 steps ({cpu_s:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": ARITH[prec],
+        "data": "synthetic (seeded three-layer Rayleigh-Taylor initial state)",
+        "config": {"workload": "three-layer RT, D2Q37, 1024x2048, tau=0.7, g=5e-5, 64 modes",
+                   "Lx": lat.Lx, "Lz": lat.Lz, "storage": "f32" if prec == "f32" else "f64",
+                   "arith": ARITH[prec], "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "working set 1.24 GB per step > 126 MB L2 (no flush needed)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": ncu_traffic(KERNEL[prec], sites),
+                     "bytes_per_site": 2 * Q * BYTES_PER_POP[prec]},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                "note": "set_populations(host) + lbm_step(1) + get_populations(host) per step"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "variants": variants,
+        "mass_after": mass,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

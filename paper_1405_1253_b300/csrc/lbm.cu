@@ -143,8 +143,8 @@ static StepParams step_params(const lbm_ctx* c) {
     p.plane = c->Lx * c->Lz;
     p.omega = 1.0 / c->tau;
     p.one_m_omega = 1.0 - 1.0 / c->tau;
-    p.us_z = -c->tau * c->grav;
-    p.T_shift = c->tau * (1.0 - c->tau) * c->grav * c->grav / DIM;
+    p.us_z = -(c->grav * c->tau);
+    p.T_shift = ((c->grav * c->grav) * c->tau) * (1.0 - c->tau) / DIM;   // exactly 0 for g = 0
     p.grav = c->grav;
     return p;
 }
