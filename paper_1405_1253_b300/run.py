@@ -1,0 +1,40 @@
+"""Command-line runner: initialise a three-layer lattice and advance it.
+
+  python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
+
+Used as the profiled program of the ncu summaries under profiles/.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import workloads as W
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--prec", default="f64_ff", choices=["f64", "f64_ff", "f32", "f32_dev"])
+    ap.add_argument("--Lx", type=int, default=1024)
+    ap.add_argument("--Lz", type=int, default=2048)
+    ap.add_argument("--tau", type=float, default=0.7)
+    ap.add_argument("--grav", type=float, default=5e-5)
+    ap.add_argument("--modes", type=int, default=64)
+    ap.add_argument("--sigma", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=3)
+    args = ap.parse_args()
+    from . import lbm
+    lat = W.Lattice(args.Lx, args.Lz, tau=args.tau, grav=args.grav, K=args.modes, sigma=args.sigma, seed=args.seed)
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=args.prec)
+    L.init_from(lat)
+    L.step(args.steps)
+    L.sync()
+    mass, energy = L.global_sums()
+    print(json.dumps({"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "mass": mass,
+                      "energy": energy}))
+    L.close()
+
+
+if __name__ == "__main__":
+    main()
