@@ -1,13 +1,17 @@
-// ff.cuh -- float-float ("double-FP32") arithmetic on the FP32 pipes.
+// ff.cuh -- float-float ("double-FP32") arithmetic on the FP32 pipes, and exact
+// conversions between binary64 bit patterns, float-float pairs and 64-bit fixed point
+// done with integer instructions only (B300 runs every FP64 conversion at the FP64 rate).
 //
 // A value is the unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2,
-// which carries a 48-bit significand.  The building blocks are the error-free
-// transformations of Knuth (two-sum) and Dekker (fast two-sum, valid for |a| >= |b|),
-// and the FMA form of the exact product a*b = p + e with e = fma(a, b, -p).  The
-// compound operations below are the usual "sloppy" double-word algorithms: their error
-// is a few units of 2^-48 relative to the magnitudes of the operands.
+// carrying a 48-bit significand.  The building blocks are the error-free transformations
+// of Knuth (two-sum) and Dekker (fast two-sum, valid for |a| >= |b|) and the FMA form of
+// the exact product a*b = p + e, e = fma(a, b, -p).  The "u" (unnormalised) variants
+// below skip the final renormalisation: their result keeps |lo| a few units of 2^-24
+// below |hi|, which every consumer here tolerates; their error is a few units of 2^-48
+// relative to the operands.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace lbm {
 
@@ -28,56 +32,92 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
     return ff{s, (a - (s - bb)) + (b - bb)};
 }
 
-__device__ __forceinline__ ff two_prod(float a, float b) {
-    const float p = a * b;
-    return ff{p, fmaf(a, b, -p)};
-}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 
+// General sum (no ordering assumed), renormalised.
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
-    ff s = two_sum(a.hi, b.hi);
+    const ff s = two_sum(a.hi, b.hi);
     return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
-
-__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 
-__device__ __forceinline__ ff ff_add_f(ff a, float b) {
-    ff s = two_sum(a.hi, b);
-    return fast_two_sum(s.hi, s.lo + a.lo);
+// Sum when |a| >= |b| is known, not renormalised.
+__device__ __forceinline__ ff ff_add_big_u(ff a, ff b) {
+    const float s = a.hi + b.hi;
+    const float e = b.hi - (s - a.hi);
+    return ff{s, e + (a.lo + b.lo)};
 }
 
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+// Product, not renormalised.
+__device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const ff t = ff_mul_u(a, b);
+    return fast_two_sum(t.hi, t.lo);
 }
 
-__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+// Product with an FP32 number (exact small integers in particular), not renormalised.
+__device__ __forceinline__ ff ff_mul_f_u(ff a, float b) {
     const float p = a.hi * b;
     float e = fmaf(a.hi, b, -p);
     e = fmaf(a.lo, b, e);
-    return fast_two_sum(p, e);
+    return ff{p, e};
 }
 
-// a * b + c
-__device__ __forceinline__ ff ff_fma(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
+__device__ __forceinline__ ff ff_renorm(ff a) { return fast_two_sum(a.hi, a.lo); }
 
-// 1 / a: FP32 seed refined by one Newton step in float-float, x1 = x0 + x0 (1 - a x0).
-__device__ __forceinline__ ff ff_rcp(ff a) {
-    const float x0 = 1.0f / a.hi;
-    const ff ax = ff_mul_f(a, x0);
-    const ff e = ff_add_f(ff_neg(ax), 1.0f);
-    return ff_add_f(ff_mul_f(e, x0), x0);
+// ---------------------------------------------------------------------------------
+// binary64 bit pattern (H = high word, L = low word) -> float-float.
+// hi = x rounded to 24 significant bits (half-up on the magnitude, by adding half of the
+// dropped 29-bit field to the pattern); lo = x - hi, whose 29-bit integer significand is
+// converted to FP32 (rounded) and scaled by 2^(E-1075).  Error <= 2^-49 |x|.
+// Valid for 2^-74 <= |x| < 2^127; smaller magnitudes (and zero) give 0.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ ff bits_to_ff(uint32_t H, uint32_t L) {
+    const uint32_t sgn = H & 0x80000000u;
+    const uint32_t Ha = H & 0x7FFFFFFFu;
+    const uint64_t m = ((((uint64_t)Ha) << 32) | L) + 0x10000000ull;
+    const uint32_t hb = (uint32_t)(m >> 29) - 0xC0000000u;        // exponent bias 1023 -> 127
+    const int32_t rem = ((int32_t)(L << 3)) >> 3;                   // x - hi in units of 2^(E-1075)
+    const uint32_t sb = ((Ha >> 20) - 948u) << 23;                  // FP32 bits of 2^(E-1075)
+    float hi = __uint_as_float(hb | sgn);
+    float lo = (float)rem * __uint_as_float(sb | sgn);
+    if (Ha < (949u << 20)) { hi = 0.f; lo = 0.f; }
+    return ff{hi, lo};
 }
 
-// Conversions through binary64.
-__device__ __forceinline__ ff ff_from_double(double x) {
-    const float hi = __double2float_rn(x);
-    return ff{hi, __double2float_rn(x - (double)hi)};
+// binary64 bit pattern -> signed 64-bit fixed point with unit 2^-60 (exact for
+// 2^-8 <= |x| < 8 up to truncation below 2^-60; |x| >= 8 is not representable).
+__device__ __forceinline__ int64_t bits_to_fix60(uint32_t H, uint32_t L) {
+    const uint32_t Ha = H & 0x7FFFFFFFu;
+    const int n = 1025 - (int)(Ha >> 20);                           // right shift of mant << 10
+    const uint64_t mant = (((uint64_t)((Ha & 0xFFFFFu) | 0x100000u)) << 42) | ((uint64_t)L << 10);
+    const uint64_t v = (n > 63) ? 0ull : (mant >> (n < 0 ? 0 : n));
+    return (H & 0x80000000u) ? -(int64_t)v : (int64_t)v;
 }
 
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+// Normalised float-float (|lo| <= ulp(hi)/2) -> binary64, rounded to nearest.
+// The pattern of (double)hi is built from the FP32 fields; lo is added as an integer
+// count of binary64 ulps of hi's binade (halved ulps when the sum drops below a power of two).
+__device__ __forceinline__ double ff_to_double_bits(ff a) {
+    const uint32_t hb = __float_as_uint(a.hi);
+    const uint32_t ha = hb & 0x7FFFFFFFu;
+    const uint32_t sgn = hb & 0x80000000u;
+    if (ha < 0x00800000u) return 0.0;                               // hi zero (or subnormal)
+    const uint32_t PH = (ha >> 3) + (896u << 20);
+    const uint32_t PL = ha << 29;
+    // scale = 2^(52 - e_hi) with the sign of hi, so that lo * scale counts magnitude ulps
+    uint32_t sbits = ((306u - (ha >> 23)) << 23) | sgn;
+    const float lo_mag_dir = a.lo * __uint_as_float(sgn | 0x3F800000u);   // lo with hi's sign removed
+    if ((ha & 0x007FFFFFu) == 0u && lo_mag_dir < 0.f) sbits += (1u << 23);   // binade below: ulp halves
+    const int32_t k = __float2int_rn(a.lo * __uint_as_float(sbits));
+    const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (int64_t)k;
+    return __hiloint2double((int)((uint32_t)(P >> 32) | sgn), (int)(uint32_t)P);
+}
 
 }  // namespace lbm
