@@ -9,6 +9,18 @@ namespace lbm {
 
 __constant__ DevLattice d_lat;
 
+// The 18 opposite velocity pairs for loops that run over pairs at run time
+// (filled from the compile-time tables of lattice.cuh at upload).
+struct PairInfo {
+    int A, B, cx, cz, c2, shell;
+};
+__constant__ PairInfo d_pairs[18];
+// Pairs are grouped by shell in canonical order: shell s owns pairs
+// [d_shell_first[s], d_shell_first[s] + d_shell_npair[s]).
+__constant__ int d_shell_first[8];
+__constant__ int d_shell_npair[8];
+__constant__ int d_vel[37][2];
+
 constexpr int DIM = 2;
 constexpr int BLOCK_Z = 128;      // threads per block along z (one site per thread)
 
@@ -46,6 +58,80 @@ __device__ __forceinline__ int pull_index(int x, int z, const int col[7], int Lz
 template <int L>
 __device__ __forceinline__ int pull_index_interior(int z, const int col[7], int plane) {
     return L * plane + col[3 - cx(L)] + z - cz(L);
+}
+
+// Tiling of one step launch (1D grid of BLOCK_Z-thread tiles):
+//   blocks [0, nwall):        wall tiles, one thread per (x, row) over the six rows
+//                             0, 1, 2, Lz-3, Lz-2, Lz-1 (half-way bounce-back applies);
+//   blocks [nwall, nwall + nzb * Lx): interior tiles, column x, rows zb*BLOCK_Z + t, aligned
+//                             to row 0 so warps store whole sectors; threads outside
+//                             3 <= z < Lz - 3 return (no wall test in this path).
+// Wall tiles come first so their scattered loads overlap with the interior work.
+struct Tiling {
+    int nwall, nzb;
+};
+inline Tiling make_tiling(int Lx, int Lz, int block) {
+    return Tiling{(6 * Lx + block - 1) / block, (Lz + block - 1) / block};
+}
+inline int tiling_blocks(const Tiling& t, int Lx) { return t.nwall + t.nzb * Lx; }
+
+struct SiteAddr {
+    int x, z, Lz, plane, Lx;
+    int col[7];            // wrap(x + k - 3) * Lz
+    // Sets x, z for this thread; false if the thread has no site.  wall: tile kind.
+    __device__ __forceinline__ bool setup(int Lx_, int Lz_, int plane_, Tiling t, bool& wall) {
+        Lx = Lx_;
+        Lz = Lz_;
+        plane = plane_;
+        const int b = blockIdx.x;
+        wall = b < t.nwall;
+        if (wall) {
+            const int i = b * blockDim.x + threadIdx.x;
+            if (i >= 6 * Lx) return false;
+            x = i / 6;
+            const int r = i - 6 * x;
+            z = r < 3 ? r : Lz - 6 + r;
+        } else {
+            const int tt = b - t.nwall;
+            x = tt / t.nzb;
+            z = (tt - x * t.nzb) * blockDim.x + threadIdx.x;
+            if (z < 3 || z >= Lz - 3) return false;
+        }
+#pragma unroll
+        for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, Lx) * Lz;
+        return true;
+    }
+    template <int L, bool WALL>
+    __device__ __forceinline__ int src() const {
+        if constexpr (WALL) return pull_index<L>(x, z, col, Lz, plane);
+        else return pull_index_interior<L>(z, col, plane);
+    }
+    // Runtime-velocity form of src() (population l with lattice vector (vx, vz)).
+    template <bool WALL>
+    __device__ __forceinline__ int src_rt(int l, int lop, int vx, int vz) const {
+        const int zs = z - vz;
+        if (WALL) {
+            if (zs < 0) return lop * plane + x * Lz + (vz - 1 - z);
+            if (zs >= Lz) return lop * plane + x * Lz + (2 * Lz - 1 - z + vz);
+        }
+        int xs = x - vx;
+        xs = xs < 0 ? xs + Lx : (xs >= Lx ? xs - Lx : xs);
+        if (Lx < 3) xs = wrap_x(x - vx, Lx);
+        return l * plane + xs * Lz + zs;
+    }
+    __device__ __forceinline__ int dst() const { return x * Lz + z; }
+};
+
+// Block-uniform decomposition of a tile: wall flag, and for interior tiles the column x
+// and the first row.  Every thread of the block computes the same values.
+__device__ __forceinline__ bool tile_is_wall(Tiling t) { return (int)blockIdx.x < t.nwall; }
+__device__ __forceinline__ int tile_column(Tiling t) { return ((int)blockIdx.x - t.nwall) / t.nzb; }
+
+// Interior tiles: sbase[l] = l * plane + wrap(x - c_lx) * Lz - c_lz, so that the pull
+// source of population l at row z is sbase[l] + z.  Filled by the first Q threads.
+__device__ __forceinline__ void fill_pull_bases(int* sbase, int x, int Lx, int Lz, int plane) {
+    const int l = threadIdx.x;
+    if (l < Q) sbase[l] = l * plane + wrap_x(x - d_vel[l][0], Lx) * Lz - d_vel[l][1];
 }
 
 // Compile-time loop: calls f(Tag<L>{}) for L = 0..N-1.

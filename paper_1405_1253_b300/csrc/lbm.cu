@@ -104,6 +104,18 @@ static int upload_lattice(int dev) {
     split_ff(h.r, h.r_hi, h.r_lo);
     split_ff(h.r2, h.r2_hi, h.r2_lo);
     CU(cudaMemcpyToSymbol(d_lat, &h, sizeof h));
+    PairInfo pairs[NPAIR];
+    for (int k = 0; k < NPAIR; k++) {
+        const int A = pair_first(k);
+        pairs[k] = PairInfo{A, opp(A), cx(A), cz(A), c2(A), shell_of(A)};
+    }
+    CU(cudaMemcpyToSymbol(d_pairs, pairs, sizeof pairs));
+    int sfirst[NSHELL] = {0}, snp[NSHELL] = {0}, vel[Q][2];
+    for (int k = NPAIR - 1; k >= 0; k--) { sfirst[shell_of(pair_first(k))] = k; snp[shell_of(pair_first(k))]++; }
+    for (int l = 0; l < Q; l++) { vel[l][0] = cx(l); vel[l][1] = cz(l); }
+    CU(cudaMemcpyToSymbol(d_shell_first, sfirst, sizeof sfirst));
+    CU(cudaMemcpyToSymbol(d_shell_npair, snp, sizeof snp));
+    CU(cudaMemcpyToSymbol(d_vel, vel, sizeof vel));
     CU(cudaDeviceSynchronize());
     g_dev_uploaded[dev] = true;
     return LBM_OK;
@@ -343,13 +355,12 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
-    dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
     for (int s = 0; s < nsteps; s++) {
         void* fin = c->buf[c->cur];
         void* fout = c->buf[c->cur ^ 1];
         switch (c->prec) {
             case LBM_F64:
-                k_step_f64<<<grid, BLOCK_Z, 0, c->stream>>>((const double*)fin, (double*)fout, p);
+                launch_step_f64((const double*)fin, (double*)fout, p, c->stream);
                 break;
             case LBM_F64_FF:
                 launch_step_ff((const double*)fin, (double*)fout, p, c->stream);

@@ -83,26 +83,24 @@ __device__ __forceinline__ void collide_f32(const float (&g)[Q], float (&fo)[Q],
     });
 }
 
-__global__ void __launch_bounds__(BLOCK_Z)
-k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p) {
-    const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
-    const int x = blockIdx.y;
-    if (z >= p.Lz) return;
-    int col[7];
-#pragma unroll
-    for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
+template <bool WALL>
+__device__ __forceinline__ void site_f32(const float* __restrict__ fin, float* __restrict__ fout,
+                                        const SiteAddr& ad, const StepParamsF& p) {
     float g[Q], fo[Q];
-    const int z0 = blockIdx.x * BLOCK_Z;
-    const bool interior = (z0 >= 3) && (z0 + BLOCK_Z + 3 <= p.Lz);
-    if (interior) {
-        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index_interior<decltype(l)::value>(z, col, p.plane)); });
-    } else {
-        static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane)); });
-    }
+    static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + ad.template src<decltype(l)::value, WALL>()); });
     collide_f32(g, fo, p);
-    const int o = x * p.Lz + z;
+    const int o = ad.dst();
 #pragma unroll
     for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
+    SiteAddr ad;
+    bool wall;
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, wall)) return;
+    if (wall) site_f32<true>(fin, fout, ad, p);
+    else site_f32<false>(fin, fout, ad, p);
 }
 
 inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, cudaStream_t st) {
@@ -111,8 +109,8 @@ inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, 
     q.omega = (float)p.omega;
     q.us_z = (float)p.us_z;
     q.T_shift = (float)p.T_shift;
-    dim3 grid((p.Lz + BLOCK_Z - 1) / BLOCK_Z, p.Lx);
-    k_step_f32<<<grid, BLOCK_Z, 0, st>>>(fin, fout, q);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    k_step_f32<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 }  // namespace lbm

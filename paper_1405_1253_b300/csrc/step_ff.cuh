@@ -8,7 +8,8 @@
 //   2. rho, J = sum c f and E = sum |c|^2 f are summed EXACTLY in 64-bit integers;
 //   3. the few per-site scalars (1/rho, u, T, the force shift) are formed in native FP64
 //      (about 30 FP64 instructions per site) and split into float-float;
-//   4. the Hermite polynomial P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh) and
+//   4. a second read of the populations (served by L1/L2, so DRAM sees each byte once) feeds
+//      the Hermite polynomial P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh) and
 //      the relaxation f' = (1 - w) g + w w_l rho P are evaluated in float-float, opposite
 //      velocities sharing the even part;
 //   5. each result is assembled back into a binary64 pattern with integer instructions.
@@ -30,16 +31,41 @@ __device__ __forceinline__ ff dsplit(double x) {
     return bits_to_ff((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x));
 }
 
-__device__ __forceinline__ void collide_ff1(const uint32_t (&H)[Q], const uint32_t (&L)[Q], double (&out)[Q],
-                                            const StepParamsFF& p) {
-    // -- exact moments in 64-bit fixed point ------------------------------------------
+// Second read of a population already read in the moment pass (served by L1/L2): issued
+// as its own instruction so the first copy need not stay live in registers.
+__device__ __forceinline__ double ld_again(const double* ptr) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(ptr));
+    return v;
+}
+
+template <bool WALL>
+__device__ __forceinline__ int pull_src(const SiteAddr& ad, const int* sbase, int l, int lop, int vx, int vz) {
+    if constexpr (WALL) return ad.template src_rt<true>(l, lop, vx, vz);
+    else return sbase[l] + ad.z;
+}
+
+template <bool WALL>
+__device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* __restrict__ fout,
+                                       const SiteAddr& ad, const int* sbase, const StepParamsFF& p) {
+    // -- pass 1: exact moments in 64-bit fixed point (all 37 loads in flight) -----------
+    auto src1 = [&](auto tag) -> int {
+        constexpr int L = decltype(tag)::value;
+        if constexpr (WALL) return ad.template src<L, true>();
+        else return sbase[L] + ad.z;
+    };
     int64_t R, Jx = 0, Jz = 0, E = 0;
     int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
-    R = bits_to_fix60(H[0], L[0]);
+    {
+        const double v0 = __ldg(fin + src1(Tag<0>{}));
+        R = bits_to_fix60((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
+    }
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        const int64_t fa = bits_to_fix60(H[A], L[A]);
-        const int64_t fb = bits_to_fix60(H[B], L[B]);
+        const double va = __ldg(fin + src1(Tag<A>{}));
+        const double vb = __ldg(fin + src1(Tag<B>{}));
+        const int64_t fa = bits_to_fix60((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
+        const int64_t fb = bits_to_fix60((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
         const int64_t ps = fa + fb, ms = fa - fb;
         S[shell_of(A)] += ps;
         if constexpr (cx(A) != 0) Jx += (int64_t)cx(A) * ms;
@@ -68,89 +94,79 @@ __device__ __forceinline__ void collide_ff1(const uint32_t (&H)[Q], const uint32
     // -- polynomial coefficients in float-float ---------------------------------------
     const ff r2 = ff_make(d_lat.r2_hi, d_lat.r2_lo);
     const ff thu2 = ff_mul(th, u2), th2 = ff_mul(th, th), u4 = ff_mul(u2, u2);
-    // k00 = 1 - u2/2 - th + u4/8 + th u2 + th^2
+    // k00 = 1 - u2/2 - th + u4/8 + th u2 + th^2; the |c|^2 coefficients carry r^2
     ff k00 = ff_add(ff_make(1.0f, 0.0f), ff_mul_f_u(u2, -0.5f));
     k00 = ff_add(k00, ff_add(ff_neg(th), ff_add(ff_mul_f_u(u4, 0.125f), ff_add(thu2, th2))));
-    // |c|^2 coefficients (|xi|^2 = r^2 |c|^2)
     const ff k01 = ff_mul(r2, ff_add(ff_mul_f_u(th, 0.5f), ff_neg(ff_add(ff_mul_f_u(thu2, 0.25f), th2))));
     const ff k02 = ff_mul(ff_mul(r2, r2), ff_mul_f_u(th2, 0.125f));
     const ff k10 = ff_add(ff_add(ff_make(1.0f, 0.0f), ff_mul_f_u(u2, -0.5f)), ff_mul_f_u(th, -2.0f));
     const ff k11 = ff_mul(r2, ff_mul_f_u(th, 0.5f));
     const ff k20 = ff_add(ff_add(ff_make(0.5f, 0.0f), ff_mul_f_u(u2, -0.25f)), ff_mul_f_u(th, -1.5f));
     const ff k21 = ff_mul(r2, ff_mul_f_u(th, 0.25f));
-    const ff a3 = ff_renorm(ff_mul_f_u(a, 3.0f)), b3 = ff_renorm(ff_mul_f_u(b, 3.0f));
     const ff om = p.one_m_omega;
-    // rest population: f' = (1-w) g + w rho w_0 k00
+    const int o = ad.dst();
+    // -- pass 2: relaxation; rolled loops over shells and their pairs keep the code in
+    //    the instruction cache, the shell coefficients are formed once per shell -------
     {
-        const ff g0 = bits_to_ff(H[0], L[0]);
+        const double v0 = ld_again(fin + src1(Tag<0>{}));
+        const ff g0 = bits_to_ff((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
         const ff W0 = ff_mul(orho, ff_make(d_lat.wf_hi[0], d_lat.wf_lo[0]));
-        out[0] = ff_to_double_bits(ff_add(ff_mul_u(om, g0), ff_mul_u(W0, k00)));
+        fout[o] = ff_to_double_bits(ff_add(ff_mul_u(om, g0), ff_mul_u(W0, k00)));
     }
-    // per-shell coefficients (general float-float sums: no ordering assumed)
-    ff K0[NSHELL], K1[NSHELL], K2[NSHELL], W[NSHELL];
-    static_for<NSHELL>([&](auto sh) {
-        constexpr int SS = decltype(sh)::value;
-        constexpr float C2 = (float)shell_c2(SS);
-        K0[SS] = ff_add(k00, ff_mul_f_u(ff_add(k01, ff_mul_f_u(k02, C2)), C2));
-        K1[SS] = ff_add(k10, ff_mul_f_u(k11, C2));
-        K2[SS] = ff_add(k20, ff_mul_f_u(k21, C2));
-        W[SS] = ff_mul(orho, ff_make(d_lat.wf_hi[SS], d_lat.wf_lo[SS]));
-    });
-    static_for<NPAIR>([&](auto k) {
-        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        constexpr int SH = shell_of(A);
-        constexpr int CX = cx(A), CZ = cz(A);
-        // s = xi_A . u_s = c_x a + c_z b
-        auto mult = [&](const ff& v, const ff& v3, int c) -> ff {
-            const int m = c < 0 ? -c : c;
-            ff t = (m == 1) ? v : (m == 2) ? ff{2.f * v.hi, 2.f * v.lo} : v3;
-            return c < 0 ? ff_neg(t) : t;
-        };
-        ff s;
-        if constexpr (CX == 0) s = mult(b, b3, CZ);
-        else if constexpr (CZ == 0) s = mult(a, a3, CX);
-        else s = ff_add(mult(a, a3, CX), mult(b, b3, CZ));
+    // Flattened loop over the 18 pairs (grouped by shell); the shell coefficients are
+    // re-formed when the shell changes, and the two populations of the next pair are
+    // requested one iteration ahead so that the reload latency overlaps the arithmetic.
+    ff K0, K1, K2, W;
+    int sh_cur = 0;
+    PairInfo pi = d_pairs[0];
+    double va = ld_again(fin + pull_src<WALL>(ad, sbase, pi.A, pi.B, pi.cx, pi.cz));
+    double vb = ld_again(fin + pull_src<WALL>(ad, sbase, pi.B, pi.A, -pi.cx, -pi.cz));
+#pragma unroll 1
+    for (int k = 0; k < NPAIR; k++) {
+        const PairInfo pn = d_pairs[k + 1 < NPAIR ? k + 1 : k];
+        const double va_n = ld_again(fin + pull_src<WALL>(ad, sbase, pn.A, pn.B, pn.cx, pn.cz));
+        const double vb_n = ld_again(fin + pull_src<WALL>(ad, sbase, pn.B, pn.A, -pn.cx, -pn.cz));
+        if (pi.shell != sh_cur) {
+            sh_cur = pi.shell;
+            const float C2 = (float)pi.c2;
+            K0 = ff_add(k00, ff_mul_f_u(ff_add(k01, ff_mul_f_u(k02, C2)), C2));
+            K1 = ff_add(k10, ff_mul_f_u(k11, C2));
+            K2 = ff_add(k20, ff_mul_f_u(k21, C2));
+            W = ff_mul(orho, ff_make(d_lat.wf_hi[sh_cur], d_lat.wf_lo[sh_cur]));
+        }
+        // s = xi_A . u_s = c_x a + c_z b (left unnormalised)
+        const ff sx = ff_mul_f_u(a, (float)pi.cx), sz = ff_mul_f_u(b, (float)pi.cz);
+        const ff st = two_sum(sx.hi, sz.hi);
+        const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
         const ff q = ff_mul_u(s, s);
         // |K0| ~ 1 > |q K2|, |K2| ~ 1/2 > q/24, |K1| ~ 1 > q/6 and |Ev| > |Od| for |u| < 0.3
-        const ff Ev = ff_add_big_u(K0[SH], ff_mul_u(q, ff_add_big_u(K2[SH], ff_mul_u(q, p.c24))));
-        const ff Od = ff_mul_u(s, ff_add_big_u(K1[SH], ff_mul_u(q, p.c6)));
-        const ff Pa = ff_mul_u(W[SH], Ev), Pb = ff_mul_u(W[SH], Od);
+        const ff Ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, ff_mul_u(q, p.c24))));
+        const ff Od = ff_mul_u(s, ff_add_big_u(K1, ff_mul_u(q, p.c6)));
+        const ff Pa = ff_mul_u(W, Ev), Pb = ff_mul_u(W, Od);
         const ff Xp = ff_add_big_u(Pa, Pb), Xm = ff_add_big_u(Pa, ff_neg(Pb));
-        const ff ga = bits_to_ff(H[A], L[A]), gb = bits_to_ff(H[B], L[B]);
-        out[A] = ff_to_double_bits(ff_add(ff_mul_u(om, ga), Xp));
-        out[B] = ff_to_double_bits(ff_add(ff_mul_u(om, gb), Xm));
-    });
+        const ff ga = bits_to_ff((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
+        const ff gb = bits_to_ff((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
+        fout[pi.A * p.plane + o] = ff_to_double_bits(ff_add(ff_mul_u(om, ga), Xp));
+        fout[pi.B * p.plane + o] = ff_to_double_bits(ff_add(ff_mul_u(om, gb), Xm));
+        pi = pn;
+        va = va_n;
+        vb = vb_n;
+    }
 }
 
-__global__ void __launch_bounds__(BLOCK_Z)
-k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p) {
-    const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
-    const int x = blockIdx.y;
-    if (z >= p.Lz) return;
-    int col[7];
-#pragma unroll
-    for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
-    uint32_t H[Q], L[Q];
-    const int z0 = blockIdx.x * BLOCK_Z;
-    const bool interior = (z0 >= 3) && (z0 + BLOCK_Z + 3 <= p.Lz);
-    if (interior) {
-        static_for<Q>([&](auto l) {
-            const double v = __ldg(fin + pull_index_interior<decltype(l)::value>(z, col, p.plane));
-            H[l.value] = (uint32_t)__double2hiint(v);
-            L[l.value] = (uint32_t)__double2loint(v);
-        });
-    } else {
-        static_for<Q>([&](auto l) {
-            const double v = __ldg(fin + pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane));
-            H[l.value] = (uint32_t)__double2hiint(v);
-            L[l.value] = (uint32_t)__double2loint(v);
-        });
+__global__ void __launch_bounds__(BLOCK_Z, 5)
+k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
+    __shared__ int sbase[Q];
+    const bool wall_tile = tile_is_wall(t);
+    if (!wall_tile) {
+        fill_pull_bases(sbase, tile_column(t), p.Lx, p.Lz, p.plane);
+        __syncthreads();
     }
-    double out[Q];
-    collide_ff1(H, L, out, p);
-    const int o = x * p.Lz + z;
-#pragma unroll
-    for (int l = 0; l < Q; l++) fout[l * p.plane + o] = out[l];
+    SiteAddr ad;
+    bool wall;
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, wall)) return;
+    if (wall) site_ff<true>(fin, fout, ad, sbase, p);
+    else site_ff<false>(fin, fout, ad, sbase, p);
 }
 
 inline ff ff_host(double v) {
@@ -169,8 +185,8 @@ inline void launch_step_ff(const double* fin, double* fout, const StepParams& p,
     q.one_m_omega = ff_host(p.one_m_omega);
     q.c24 = ff_host(1.0 / 24.0);
     q.c6 = ff_host(1.0 / 6.0);
-    dim3 grid((p.Lz + BLOCK_Z - 1) / BLOCK_Z, p.Lx);
-    k_step_ff<<<grid, BLOCK_Z, 0, st>>>(fin, fout, q);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    k_step_ff<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 }  // namespace lbm
