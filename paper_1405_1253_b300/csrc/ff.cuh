@@ -84,21 +84,32 @@ __device__ __forceinline__ ff bits_to_ff(uint32_t H, uint32_t L) {
     const uint64_t m = ((((uint64_t)Ha) << 32) | L) + 0x10000000ull;
     const uint32_t hb = (uint32_t)(m >> 29) - 0xC0000000u;        // exponent bias 1023 -> 127
     const int32_t rem = ((int32_t)(L << 3)) >> 3;                   // x - hi in units of 2^(E-1075)
-    const uint32_t sb = ((Ha >> 20) - 948u) << 23;                  // FP32 bits of 2^(E-1075)
-    float hi = __uint_as_float(hb | sgn);
-    float lo = (float)rem * __uint_as_float(sb | sgn);
-    if (Ha < (949u << 20)) { hi = 0.f; lo = 0.f; }
+    // FP32 bits of 2^(E-1075): (E - 948) << 23, i.e. E * 2^23 - 948 * 2^23 modulo 2^32
+    const uint32_t sb = (Ha >> 20) * 0x00800000u + 0x26000000u;
+    const bool ok = Ha >= (949u << 20);                              // |x| >= 2^-74
+    const float hi = __uint_as_float(ok ? (hb | sgn) : 0u);
+    const float lo = (float)(ok ? rem : 0) * __uint_as_float(sb | sgn);
     return ff{hi, lo};
 }
 
 // binary64 bit pattern -> signed 64-bit fixed point with unit 2^-60 (exact for
-// 2^-8 <= |x| < 8 up to truncation below 2^-60; |x| >= 8 is not representable).
+// 2^-8 <= |x| < 4, truncated below 2^-60 for smaller |x|; |x| >= 4 is not representable).
 __device__ __forceinline__ int64_t bits_to_fix60(uint32_t H, uint32_t L) {
     const uint32_t Ha = H & 0x7FFFFFFFu;
-    const int n = 1025 - (int)(Ha >> 20);                           // right shift of mant << 10
-    const uint64_t mant = (((uint64_t)((Ha & 0xFFFFFu) | 0x100000u)) << 42) | ((uint64_t)L << 10);
-    const uint64_t v = (n > 63) ? 0ull : (mant >> (n < 0 ? 0 : n));
-    return (H & 0x80000000u) ? -(int64_t)v : (int64_t)v;
+    const uint32_t n = 1025u - (Ha >> 20);                          // right shift of mant << 10
+    // significand << 10 as two words: top 21 bits + the low word's top 22 bits, low word << 10
+    const uint32_t mh = __funnelshift_l(L, (Ha & 0x000FFFFFu) | 0x00100000u, 10);
+    const uint32_t ml = L << 10;
+    uint32_t vh, vl;
+    if (n < 32u) {                                                  // |x| >= 2^-22 (the usual case)
+        vl = __funnelshift_r(ml, mh, n);
+        vh = mh >> n;
+    } else {                                                        // tiny (or |x| >= 8: n wraps)
+        vl = n < 64u ? (mh >> (n - 32u)) : 0u;
+        vh = 0u;
+    }
+    const int64_t v = (int64_t)(((uint64_t)vh << 32) | vl);
+    return (H & 0x80000000u) ? -v : v;
 }
 
 // Normalised float-float (|lo| <= ulp(hi)/2) -> binary64, rounded to nearest.
@@ -108,16 +119,18 @@ __device__ __forceinline__ double ff_to_double_bits(ff a) {
     const uint32_t hb = __float_as_uint(a.hi);
     const uint32_t ha = hb & 0x7FFFFFFFu;
     const uint32_t sgn = hb & 0x80000000u;
-    if (ha < 0x00800000u) return 0.0;                               // hi zero (or subnormal)
     const uint32_t PH = (ha >> 3) + (896u << 20);
     const uint32_t PL = ha << 29;
-    // scale = 2^(52 - e_hi) with the sign of hi, so that lo * scale counts magnitude ulps
-    uint32_t sbits = ((306u - (ha >> 23)) << 23) | sgn;
-    const float lo_mag_dir = a.lo * __uint_as_float(sgn | 0x3F800000u);   // lo with hi's sign removed
-    if ((ha & 0x007FFFFFu) == 0u && lo_mag_dir < 0.f) sbits += (1u << 23);   // binade below: ulp halves
+    // scale 2^(52 - e_hi) carrying hi's sign: FP32 bits (306 - E8) << 23, E8 = hi's biased exponent
+    uint32_t sbits = (0x99000000u - (ha & 0x7F800000u)) | sgn;
+    // the sum drops into the binade below when hi is a power of two and lo points towards zero
+    if ((ha & 0x007FFFFFu) == 0u && ((__float_as_uint(a.lo) ^ hb) & 0x80000000u) && a.lo != 0.f)
+        sbits += (1u << 23);
     const int32_t k = __float2int_rn(a.lo * __uint_as_float(sbits));
-    const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (int64_t)k;
-    return __hiloint2double((int)((uint32_t)(P >> 32) | sgn), (int)(uint32_t)P);
+    const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (uint64_t)(int64_t)k;
+    const uint32_t outH = ha >= 0x00800000u ? ((uint32_t)(P >> 32) | sgn) : 0u;
+    const uint32_t outL = ha >= 0x00800000u ? (uint32_t)P : 0u;
+    return __hiloint2double((int)outH, (int)outL);
 }
 
 }  // namespace lbm

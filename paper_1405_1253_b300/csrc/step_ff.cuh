@@ -8,11 +8,11 @@
 //   2. rho, J = sum c f and E = sum |c|^2 f are summed EXACTLY in 64-bit integers;
 //   3. the few per-site scalars (1/rho, u, T, the force shift) are formed in native FP64
 //      (about 30 FP64 instructions per site) and split into float-float;
-//   4. a second read of the populations (served by L1/L2, so DRAM sees each byte once) feeds
-//      the Hermite polynomial P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh) and
-//      the relaxation f' = (1 - w) g + w w_l rho P are evaluated in float-float, opposite
-//      velocities sharing the even part;
-//   5. each result is assembled back into a binary64 pattern with integer instructions.
+//   4. w f^eq_l = w w_l rho P(s), P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh),
+//      is evaluated in float-float, opposite velocities sharing the even part, and
+//      assembled into a binary64 pattern with integer instructions;
+//   5. a second read of the populations (served by L1/L2, so DRAM sees each byte once)
+//      gives f' = (1 - w) g + w f^eq with one FP64 FMA per population.
 #pragma once
 #include "common.cuh"
 #include "ff.cuh"
@@ -22,7 +22,7 @@ namespace lbm {
 struct StepParamsFF {
     int Lx, Lz, plane;
     double omega, us_z, T_shift;   // FP64 per-site stage
-    ff one_m_omega;                // float-float per-population stage
+    double one_m_omega_d;          // the final f' = (1 - w) g + w f^eq is one FP64 FMA
     ff c24, c6;                    // 1/24 and 1/6
 };
 
@@ -103,15 +103,13 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     const ff k11 = ff_mul(r2, ff_mul_f_u(th, 0.5f));
     const ff k20 = ff_add(ff_add(ff_make(0.5f, 0.0f), ff_mul_f_u(u2, -0.25f)), ff_mul_f_u(th, -1.5f));
     const ff k21 = ff_mul(r2, ff_mul_f_u(th, 0.25f));
-    const ff om = p.one_m_omega;
     const int o = ad.dst();
     // -- pass 2: relaxation; rolled loops over shells and their pairs keep the code in
     //    the instruction cache, the shell coefficients are formed once per shell -------
     {
         const double v0 = ld_again(fin + src1(Tag<0>{}));
-        const ff g0 = bits_to_ff((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
         const ff W0 = ff_mul(orho, ff_make(d_lat.wf_hi[0], d_lat.wf_lo[0]));
-        fout[o] = ff_to_double_bits(ff_add(ff_mul_u(om, g0), ff_mul_u(W0, k00)));
+        fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
     }
     // Flattened loop over the 18 pairs (grouped by shell); the shell coefficients are
     // re-formed when the shell changes, and the two populations of the next pair are
@@ -128,14 +126,14 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const double vb_n = ld_again(fin + pull_src<WALL>(ad, sbase, pn.B, pn.A, -pn.cx, -pn.cz));
         if (pi.shell != sh_cur) {
             sh_cur = pi.shell;
-            const float C2 = (float)pi.c2;
+            const float C2 = pi.fc2;
             K0 = ff_add(k00, ff_mul_f_u(ff_add(k01, ff_mul_f_u(k02, C2)), C2));
             K1 = ff_add(k10, ff_mul_f_u(k11, C2));
             K2 = ff_add(k20, ff_mul_f_u(k21, C2));
             W = ff_mul(orho, ff_make(d_lat.wf_hi[sh_cur], d_lat.wf_lo[sh_cur]));
         }
         // s = xi_A . u_s = c_x a + c_z b (left unnormalised)
-        const ff sx = ff_mul_f_u(a, (float)pi.cx), sz = ff_mul_f_u(b, (float)pi.cz);
+        const ff sx = ff_mul_f_u(a, pi.fcx), sz = ff_mul_f_u(b, pi.fcz);
         const ff st = two_sum(sx.hi, sz.hi);
         const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
         const ff q = ff_mul_u(s, s);
@@ -143,11 +141,11 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const ff Ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, ff_mul_u(q, p.c24))));
         const ff Od = ff_mul_u(s, ff_add_big_u(K1, ff_mul_u(q, p.c6)));
         const ff Pa = ff_mul_u(W, Ev), Pb = ff_mul_u(W, Od);
-        const ff Xp = ff_add_big_u(Pa, Pb), Xm = ff_add_big_u(Pa, ff_neg(Pb));
-        const ff ga = bits_to_ff((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
-        const ff gb = bits_to_ff((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
-        fout[pi.A * p.plane + o] = ff_to_double_bits(ff_add(ff_mul_u(om, ga), Xp));
-        fout[pi.B * p.plane + o] = ff_to_double_bits(ff_add(ff_mul_u(om, gb), Xm));
+        // w f^eq of the pair in binary64, then f' = (1 - w) g + w f^eq by one FP64 FMA each
+        const double Xp = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, Pb)));
+        const double Xm = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, ff_neg(Pb))));
+        fout[pi.A * p.plane + o] = fma(p.one_m_omega_d, va, Xp);
+        fout[pi.B * p.plane + o] = fma(p.one_m_omega_d, vb, Xm);
         pi = pn;
         va = va_n;
         vb = vb_n;
@@ -182,7 +180,7 @@ inline void launch_step_ff(const double* fin, double* fout, const StepParams& p,
     q.omega = p.omega;
     q.us_z = p.us_z;
     q.T_shift = p.T_shift;
-    q.one_m_omega = ff_host(p.one_m_omega);
+    q.one_m_omega_d = p.one_m_omega;
     q.c24 = ff_host(1.0 / 24.0);
     q.c6 = ff_host(1.0 / 6.0);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
