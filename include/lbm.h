@@ -168,6 +168,25 @@ int lbm_sync(lbm_ctx *c);
  * c (37 x 2 ints, canonical order), w (37 doubles), r.  Any pointer may be NULL.      */
 int lbm_lattice(int *c, double *w, double *r);
 
+/* Horizontal mean T(z) of an FP64 population array, allocating nothing.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they need the diagnostic -- a plugin whose device memory
+ * is all handed to it by a host application, code whose memory belongs to a pool or
+ * budget it does not control, or a latency-critical loop where cudaMalloc's implicit
+ * device synchronisation is not acceptable -- and so cannot create an lbm_ctx
+ * (lbm_create allocates scratch) or let lbm_row_mean_T grow its reduction buffer.
+ * f: device array of 37*Lx*Lz doubles in the storage layout; Tbar: device array of Lz
+ * doubles (output); both on the current device; cuda_stream: cudaStream_t or NULL.
+ * The two-stage reduction of lbm_row_mean_T runs with its partial sums in one static
+ * device array of 2^20 doubles (8 MiB) that every GPU loading the library keeps until
+ * process exit; Lz above 1,048,576 is rejected with LBM_EINVAL.  The partial sums are
+ * fully rewritten by every call, so nothing needs clearing; but all calls on a device
+ * share that array, so calls that may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The first call on a device does
+ * a one-time set-up (lattice constants, scratch address) with host synchronisation, so
+ * make it before any stream capture.  Calls no cudaMalloc/cudaFree.  Asynchronous.    */
+int lbm_row_mean_T_noalloc(const double *f, int Lx, int Lz, double *Tbar, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none).                        */
 const char *lbm_last_error(void);
 

@@ -596,3 +596,65 @@ int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Allocation-free horizontal mean of T (lbm_row_mean_T_noalloc).
+//
+// For callers that must not allocate device memory: the two-stage reduction of
+// lbm_row_mean_T keeps its per-chunk partial sums in this file-scope array instead of
+// context scratch.  Host code cannot use the array's name as a device address; the
+// address is taken once per device with cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------------
+#define LBM_NOALLOC_SCRATCH_DOUBLES (1 << 20)   /* 8 MiB per device, held until exit */
+
+static __device__ __align__(256) double g_rowT_scratch[LBM_NOALLOC_SCRATCH_DOUBLES];
+
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[128];
+
+// Per-device set-up: lattice constants and the scratch address (no allocation).
+static int noalloc_setup(int dev, double** out) {
+    if (dev < 0 || dev >= 128) return fail(LBM_EINVAL, "device index %d out of range", dev);
+    int rc = upload_lattice(dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rowT_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(LBM_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LBM_OK;
+}
+
+extern "C" int lbm_row_mean_T_noalloc(const double* f, int Lx, int Lz, double* Tbar, void* cuda_stream) {
+    if (!f || !Tbar) return fail(LBM_EINVAL, "NULL argument");
+    if (Lx < 1 || Lz < 1) return fail(LBM_EINVAL, "lattice %d x %d: need Lx >= 1, Lz >= 1", Lx, Lz);
+    if (Lz > LBM_NOALLOC_SCRATCH_DOUBLES)
+        return fail(LBM_EINVAL, "Lz = %d exceeds the static scratch of %d rows", Lz, LBM_NOALLOC_SCRATCH_DOUBLES);
+    if ((long long)Q * Lx * Lz >= (1LL << 31))
+        return fail(LBM_EINVAL, "lattice %d x %d too large: 37*Lx*Lz must be < 2^31", Lx, Lz);
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    cudaPointerAttributes af, at;
+    CU(cudaPointerGetAttributes(&af, f));
+    CU(cudaPointerGetAttributes(&at, Tbar));
+    if (af.type != cudaMemoryTypeDevice || at.type != cudaMemoryTypeDevice || af.device != dev || at.device != dev)
+        return fail(LBM_EINVAL, "f and Tbar must be device memory on the current device %d", dev);
+    double* scratch = nullptr;
+    int rc = noalloc_setup(dev, &scratch);
+    if (rc) return rc;
+    // same chunking as lbm_row_mean_T, bounded by the static scratch
+    const int target = std::max(1, std::min((148 * 16 * 128) / Lz, LBM_NOALLOC_SCRATCH_DOUBLES / Lz));
+    const int nx_per = (Lx + std::min(Lx, target) - 1) / std::min(Lx, target);
+    const int nch = (Lx + nx_per - 1) / nx_per;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    dim3 grid((Lz + 127) / 128, nch);
+    k_rowT_partial<StoreF64><<<grid, 128, 0, st>>>(f, nullptr, Lx, Lz, nx_per, scratch);
+    LAUNCH_CHECK();
+    k_rowT_final<<<(Lz + 127) / 128, 128, 0, st>>>(scratch, nch, Lx, Lz, Tbar);
+    LAUNCH_CHECK();
+    return LBM_OK;
+}

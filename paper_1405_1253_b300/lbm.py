@@ -53,6 +53,7 @@ _SIGS = {
     "lbm_init_adjoint": (_i, [_vp, ctypes.POINTER(LayersDesc), _vp, _dp, _dp]),
     "lbm_sync": (_i, [_vp]),
     "lbm_lattice": (_i, [_ip, _dp, _dp]),
+    "lbm_row_mean_T_noalloc": (_i, [_vp, _i, _i, _vp, _vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -88,6 +89,11 @@ def lattice():
     r = np.zeros(1)
     _check(_lib.lbm_lattice(c.ctypes.data_as(_ip), _dptr(w), _dptr(r)))
     return c.reshape(Q, 2), w, float(r[0])
+
+
+def row_mean_T_noalloc(f_dev_ptr: int, Lx: int, Lz: int, Tbar_dev_ptr: int, stream_ptr: int = 0):
+    """Allocation-free horizontal mean of T of an FP64 population array (device pointers)."""
+    _check(_lib.lbm_row_mean_T_noalloc(f_dev_ptr, int(Lx), int(Lz), Tbar_dev_ptr, stream_ptr or None))
 
 
 def layers_desc(T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi):
