@@ -1,0 +1,149 @@
+"""Gradient of the mixing-layer widths with respect to the interface-mode amplitudes.
+
+The loss is L = L_u + L_d, the threshold widths of the two fronts (Sec. IV) at step N of
+the three-layer run started from the perturbed initial state (Sec. I).  The forward pass
+runs N fused steps, keeping every K-th state as a device checkpoint.  The backward pass
+starts from lam_N = dL/df_N (width adjoint -> mean profile -> T -> f), then, segment by
+segment from the last, recomputes the K states of the segment from its checkpoint into a
+device buffer and applies the adjoint step K times (lam_t = P^T J_C^T lam_{t+1}); the
+adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA library;
+this module only orders the calls and owns the buffers (through PyTorch).
+
+Memory: (N/K) checkpoints + K segment states + 2 adjoint fields, each 37 Lx Lz doubles.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbm as _lbm
+from .workloads import Lattice as LatticeDesc
+
+Q = 37
+
+
+@dataclass
+class AdjointStats:
+    forward_s: float = 0.0
+    backward_s: float = 0.0
+    recompute_steps: int = 0
+    adjoint_steps: int = 0
+    checkpoint_bytes: int = 0
+    segment_bytes: int = 0
+    state_bytes: int = 0
+    widths: np.ndarray = field(default_factory=lambda: np.zeros(2))
+
+
+class WidthGradient:
+    """Forward/backward driver for one lattice description (FP64 context)."""
+
+    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int):
+        import torch
+        if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
+            raise ValueError("nsteps must be a positive multiple of ckpt")
+        self.torch = torch
+        self.lat = lat
+        self.N = int(nsteps)
+        self.K = int(ckpt)
+        self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64")
+        n = Q * lat.Lx * lat.Lz
+        dev = self.L.device
+        self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]
+        self.seg = torch.empty((self.K, n), dtype=torch.float64, device=dev)
+        self.lam = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=8 * n * self.K,
+                                  state_bytes=8 * n)
+        self._amps = None
+
+    def _init(self, amp_lo, amp_hi):
+        m = self.lat.modes()
+        lat = self.lat
+        self.L.init_layers(lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi, lat.rho_ref, lat.tanh_w,
+                           amp_lo, m.ph_lo, amp_hi, m.ph_hi)
+
+    def forward(self, amp_lo, amp_hi) -> float:
+        """Run N steps from the initial state with these amplitudes; returns L_u + L_d."""
+        torch = self.torch
+        lat = self.lat
+        amp_lo = np.asarray(amp_lo, dtype=np.float64)
+        amp_hi = np.asarray(amp_hi, dtype=np.float64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self._init(amp_lo, amp_hi)
+        for s in range(self.N // self.K):
+            self.L.populations_device(self.ckpts[s])
+            self.L.step(self.K)
+        widths, dL = self.L.widths(lat.T_u, lat.T_m, lat.T_d, with_grad=True)
+        self.stats.forward_s = time.perf_counter() - t0
+        self.stats.widths = widths
+        self._amps = (amp_lo, amp_hi)
+        self._dL = dL
+        self._fN = self.L.populations_device()
+        return float(widths.sum())
+
+    def backward(self, grad_out: float = 1.0):
+        """dL/damp_lo, dL/damp_hi for the last forward call (scaled by grad_out)."""
+        torch = self.torch
+        lat = self.lat
+        if self._amps is None:
+            raise RuntimeError("backward before forward")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cur, nxt = self.lam
+        self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
+        for s in range(self.N // self.K - 1, -1, -1):
+            # recompute the K states f_{sK} .. f_{sK+K-1} of this segment
+            self.L.set_populations(self.ckpts[s])
+            for j in range(self.K):
+                self.L.populations_device(self.seg[j])
+                if j + 1 < self.K:
+                    self.L.step(1)
+            self.stats.recompute_steps += self.K - 1
+            for j in range(self.K - 1, -1, -1):
+                self.L.adjoint_step(self.seg[j], cur, nxt)
+                cur, nxt = nxt, cur
+            self.stats.adjoint_steps += self.K
+        amp_lo, amp_hi = self._amps
+        m = lat.modes()
+        g_lo, g_hi = self.L.init_adjoint(cur, lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi, lat.rho_ref,
+                                         lat.tanh_w, amp_lo, m.ph_lo, amp_hi, m.ph_hi)
+        self.stats.backward_s = time.perf_counter() - t0
+        return g_lo, g_hi
+
+    def close(self):
+        self.L.close()
+
+
+def _make_function():
+    import torch
+
+    class WidthLoss(torch.autograd.Function):
+        """torch.autograd.Function: (amp_lo, amp_hi) -> L_u + L_d at step N."""
+
+        @staticmethod
+        def forward(ctx, amp_lo, amp_hi, driver: WidthGradient):
+            val = driver.forward(amp_lo.detach().cpu().numpy(), amp_hi.detach().cpu().numpy())
+            ctx.driver = driver
+            ctx.dtype, ctx.device = amp_lo.dtype, amp_lo.device
+            return torch.tensor(val, dtype=amp_lo.dtype, device=amp_lo.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            g_lo, g_hi = ctx.driver.backward(float(grad))
+            mk = lambda a: torch.as_tensor(a, dtype=ctx.dtype, device=ctx.device)
+            return mk(g_lo), mk(g_hi), None
+
+    return WidthLoss
+
+
+_WidthLoss = None
+
+
+def width_loss(amp_lo, amp_hi, driver: WidthGradient):
+    """Differentiable L_u + L_d (torch tensors of mode amplitudes in, scalar tensor out)."""
+    global _WidthLoss
+    if _WidthLoss is None:
+        _WidthLoss = _make_function()
+    return _WidthLoss.apply(amp_lo, amp_hi, driver)

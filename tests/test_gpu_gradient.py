@@ -1,0 +1,83 @@
+"""Gradient of the two fronts' mixing widths with respect to the interface-mode amplitudes:
+the checkpointed GPU adjoint against the oracle's adjoint chain (tiny lattice) and against
+centred finite differences of the GPU forward (relative 1e-4, step 1e-6)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_1253_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def adj():
+    from paper_1405_1253_b300 import adjoint
+    return adjoint
+
+
+def test_gradient_matches_oracle_chain(adj):
+    lat = W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=21)
+    nsteps, ckpt = 6, 3
+    drv = adj.WidthGradient(lat, nsteps, ckpt)
+    m = lat.modes()
+    Lval = drv.forward(m.amp_lo, m.amp_hi)
+    g_lo, g_hi = drv.backward()
+    drv.close()
+    a = lat.layer_args()
+    states = [oracle.init_layers(lat.Lx, lat.Lz, **a)]
+    for _ in range(nsteps):
+        states.append(oracle.step(states[-1], lat.tau, lat.grav))
+    Lo, dL = oracle.widths(oracle.row_mean_T(states[-1]), lat.T_u, lat.T_m, lat.T_d, with_grad=True)
+    assert abs(Lval - Lo.sum()) < 1e-10 * abs(Lo.sum())
+    lam = oracle.loss_adjoint(states[-1], dL)
+    for t in range(nsteps - 1, -1, -1):
+        lam = oracle.adjoint_step(states[t], lam, lat.tau, lat.grav)
+    o_lo, o_hi = oracle.init_adjoint(lat.Lx, lat.Lz, **a, lam0=lam)
+    np.testing.assert_allclose(g_lo, o_lo, rtol=1e-9, atol=1e-12 * np.abs(o_lo).max())
+    np.testing.assert_allclose(g_hi, o_hi, rtol=1e-9, atol=1e-12 * np.abs(o_hi).max())
+
+
+def fd_gradient(drv, lat, h, ks):
+    m = lat.modes()
+    fd_lo, fd_hi = np.zeros(lat.K), np.zeros(lat.K)
+    for k in ks:
+        e = np.zeros(lat.K)
+        e[k] = h
+        fd_lo[k] = (drv.forward(m.amp_lo + e, m.amp_hi) - drv.forward(m.amp_lo - e, m.amp_hi)) / (2 * h)
+        fd_hi[k] = (drv.forward(m.amp_lo, m.amp_hi + e) - drv.forward(m.amp_lo, m.amp_hi - e)) / (2 * h)
+    return fd_lo, fd_hi
+
+
+def fd_check(adj, lat, nsteps, ckpt, tol=1e-4):
+    """Adjoint gradient (through torch.autograd) against centred differences:
+    normwise relative error < tol with step 1e-6, and componentwise relative error < tol
+    with step 1e-4 (at 1e-6 the forward's ~1e-12 rounding noise in L becomes ~1e-6 in each
+    difference quotient, which only the normwise measure averages out)."""
+    import torch
+    drv = adj.WidthGradient(lat, nsteps, ckpt)
+    m = lat.modes()
+    amp_lo = torch.tensor(m.amp_lo, requires_grad=True)
+    amp_hi = torch.tensor(m.amp_hi, requires_grad=True)
+    loss = adj.width_loss(amp_lo, amp_hi, drv)
+    loss.backward()
+    g = np.concatenate([amp_lo.grad.numpy(), amp_hi.grad.numpy()])
+    fd6 = np.concatenate(fd_gradient(drv, lat, 1e-6, range(lat.K)))
+    assert np.linalg.norm(g - fd6) / np.linalg.norm(fd6) < tol
+    fd4 = np.concatenate(fd_gradient(drv, lat, 1e-4, range(lat.K)))
+    scale = np.maximum(np.abs(fd4), 1e-3 * np.abs(fd4).max())
+    assert np.max(np.abs(g - fd4) / scale) < tol
+    drv.close()
+    return g
+
+
+def test_gradient_vs_finite_differences_small(adj):
+    lat = W.Lattice(64, 192, tau=0.8, grav=1e-4, K=4, sigma=1.0, seed=22)
+    fd_check(adj, lat, nsteps=200, ckpt=20)
+
+
+def test_gradient_vs_finite_differences_256x512_2000_steps(adj):
+    """The differentiation workload: 256x512, 2000 steps, checkpoint every 100, 16 modes
+    per front, centred differences on every amplitude."""
+    lat = W.GRADIENT_256x512
+    fd_check(adj, lat, nsteps=W.GRADIENT_STEPS, ckpt=W.GRADIENT_CKPT)
