@@ -168,6 +168,49 @@ int lbm_sync(lbm_ctx *c);
  * c (37 x 2 ints, canonical order), w (37 doubles), r.  Any pointer may be NULL.      */
 int lbm_lattice(int *c, double *w, double *r);
 
+/* ---------------------------------------------------------------------------------
+ * Ensembles: independent lattices (the paper's N_conf realisations of one setup, Table
+ * II) advanced together.  An ensemble groups existing contexts that share device,
+ * precision (LBM_F64_FF or LBM_F32), tau, g and stream; each keeps its own buffers and
+ * sizes.  Results are identical to stepping each context alone.
+ * ------------------------------------------------------------------------------- */
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* Group n contexts (borrowed; they must outlive the ensemble).                        */
+int lbm_ensemble_create(lbm_ensemble **out, int n, lbm_ctx *const *ctxs);
+int lbm_ensemble_destroy(lbm_ensemble *e);
+
+/* Launch shape: mode 0 = one launch per step over the tiles of all lattices; mode 1 =
+ * one persistent cooperative launch for all steps, CTAs taking (step, tile) items from
+ * a step-major queue with a per-lattice step barrier (a tile of step s waits until all
+ * tiles of step s-1 of its lattice are done).  tile_z: threads (rows) per tile, 64, 128
+ * or 256.  ctas_per_sm: persistent CTAs per SM (0: as many as fit).                   */
+int lbm_ensemble_config(lbm_ensemble *e, int mode, int tile_z, int ctas_per_sm);
+
+/* Autotuner: times `steps` steps (after a warm-up of the same length) for every mode,
+ * tile_z and CTA count, keeps the fastest and reports it (any output may be NULL;
+ * best_ms per step).  The trial runs advance the lattices' state.                     */
+int lbm_ensemble_tune(lbm_ensemble *e, int steps, double *best_ms, int *best_mode, int *best_tile_z,
+                      int *best_ctas_per_sm);
+
+/* Advance every lattice by nsteps (asynchronous on the shared stream).                */
+int lbm_ensemble_step(lbm_ensemble *e, int nsteps);
+
+/* Capture one lbm_ensemble_step(e, nsteps) into a CUDA graph (the stream must not be the
+ * legacy default stream); lbm_ensemble_graph_launch replays it.  A replay requires every
+ * lattice to be in the buffer it was in at capture (always true for even nsteps).      */
+int lbm_ensemble_capture(lbm_ensemble *e, int nsteps);
+int lbm_ensemble_graph_launch(lbm_ensemble *e);
+
+/* Wait for the stream; LBM_ETIMEOUT if a persistent launch's bounded barrier wait ran
+ * out (the error word is then cleared).                                                */
+int lbm_ensemble_sync(lbm_ensemble *e);
+
+/* Bounded-wait parameters of the persistent launch: the cycle budget of one barrier wait
+ * (default 4e9, about 2 s) and an extra count added to every barrier target (default 0;
+ * a positive value makes every wait run out, for testing the timeout path).            */
+int lbm_ensemble_set_wait(lbm_ensemble *e, long long spin_limit_cycles, unsigned int extra_wait);
+
 /* Horizontal mean T(z) of an FP64 population array, allocating nothing.
  * The paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory when they need the diagnostic -- a plugin whose device memory

@@ -79,12 +79,11 @@ inline int tiling_blocks(const Tiling& t, int Lx) { return t.nwall + t.nzb * Lx;
 struct SiteAddr {
     int x, z, Lz, plane, Lx;
     int col[7];            // wrap(x + k - 3) * Lz
-    // Sets x, z for this thread; false if the thread has no site.  wall: tile kind.
-    __device__ __forceinline__ bool setup(int Lx_, int Lz_, int plane_, Tiling t, bool& wall) {
+    // Sets x, z for this thread of tile b; false if the thread has no site.  wall: tile kind.
+    __device__ __forceinline__ bool setup(int Lx_, int Lz_, int plane_, Tiling t, int b, bool& wall) {
         Lx = Lx_;
         Lz = Lz_;
         plane = plane_;
-        const int b = blockIdx.x;
         wall = b < t.nwall;
         if (wall) {
             const int i = b * blockDim.x + threadIdx.x;
@@ -125,8 +124,31 @@ struct SiteAddr {
 
 // Block-uniform decomposition of a tile: wall flag, and for interior tiles the column x
 // and the first row.  Every thread of the block computes the same values.
-__device__ __forceinline__ bool tile_is_wall(Tiling t) { return (int)blockIdx.x < t.nwall; }
-__device__ __forceinline__ int tile_column(Tiling t) { return ((int)blockIdx.x - t.nwall) / t.nzb; }
+__device__ __forceinline__ bool tile_is_wall(Tiling t, int b) { return b < t.nwall; }
+__device__ __forceinline__ int tile_column(Tiling t, int b) { return (b - t.nwall) / t.nzb; }
+
+// Load policies.  LoadNC: read-only path (populations written by an earlier launch).
+// LoadCG: L2-coherent loads, for data written earlier in the same launch by other CTAs
+// (the persistent ensemble kernel), which the per-SM L1 could hold stale copies of.
+struct LoadNC {
+    template <class T>
+    __device__ static __forceinline__ T ld(const T* p) { return __ldg(p); }
+    // a second read issued as its own instruction (not merged with an earlier one)
+    __device__ static __forceinline__ double ld_again(const double* p) {
+        double v;
+        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
+};
+struct LoadCG {
+    template <class T>
+    __device__ static __forceinline__ T ld(const T* p) { return __ldcg(p); }
+    __device__ static __forceinline__ double ld_again(const double* p) {
+        double v;
+        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
+};
 
 // Interior tiles: sbase[l] = l * plane + wrap(x - c_lx) * Lz - c_lz, so that the pull
 // source of population l at row z is sbase[l] + z.  Filled by the first Q threads.

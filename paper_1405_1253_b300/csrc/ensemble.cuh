@@ -1,0 +1,150 @@
+// ensemble.cuh -- many independent lattices (the paper's N_conf realisations, Table II)
+// advanced together.
+//
+// Every lattice keeps its own two population buffers and its own tiling (wall tiles, then
+// interior tiles, see common.cuh); the tiles of all lattices are numbered consecutively
+// (lattice i owns tiles [tile_begin_i, tile_begin_i + ntiles_i)).  Two launch shapes:
+//   k_ens_step:       one launch per time step over all tiles of all lattices (the launch
+//                     boundary separates the steps);
+//   k_ens_persistent: ONE launch for n steps.  Co-resident CTAs (cooperative launch) take
+//                     work items (step, tile) from a step-major queue; before a tile of
+//                     step s of lattice i runs, the CTA waits until all tiles of step s-1 of
+//                     lattice i are done (per-lattice step barrier: a completion counter).
+//                     The wait is a bounded spin: past the limit it sets the error word and
+//                     the CTA leaves, and every other CTA leaves at its next wait.  Data
+//                     written inside the launch is read through L2 (LoadCG), never a stale L1.
+// Progress of the persistent kernel: all CTAs are resident and items are handed out in
+// increasing order, while every item depends only on items of the previous step (smaller
+// numbers), so the smallest blocked item always has all of its dependencies running.
+#pragma once
+#include "common.cuh"
+#include "step_f32.cuh"
+#include "step_ff.cuh"
+
+namespace lbm {
+
+struct EnsLattice {
+    void* buf[2];
+    int Lx, Lz, plane;
+    int cur;          // buffer holding the state before the launch's first step
+    Tiling t;
+    int tile_begin;   // first global tile number
+    int ntiles;
+};
+
+struct EnsControl {   // device words, reset before every persistent launch
+    unsigned int queue;
+    unsigned int err;
+    unsigned int pad[2];
+};
+
+// Lattice owning global tile b (binary search over tile_begin; n <= a few hundred).
+__device__ __forceinline__ int ens_find(const EnsLattice* __restrict__ lats, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (lats[mid].tile_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Physics shared by all lattices; per-lattice sizes are filled in per tile.
+template <class P>
+__device__ __forceinline__ P with_shape(P q, const EnsLattice& L) {
+    q.Lx = L.Lx;
+    q.Lz = L.Lz;
+    q.plane = L.plane;
+    return q;
+}
+
+// One tile of one lattice at step s of the launch (buffers chosen by parity).
+template <class LD>
+__device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, const StepParamsFF& qf,
+                                        int* sbase) {
+    const double* fin = (const double*)L.buf[(L.cur + s) & 1];
+    double* fout = (double*)L.buf[(L.cur + s + 1) & 1];
+    tile_ff<LD>(fin, fout, with_shape(qf, L), L.t, local, sbase);
+}
+template <class LD>
+__device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, const StepParamsF& qs, int*) {
+    const float* fin = (const float*)L.buf[(L.cur + s) & 1];
+    float* fout = (float*)L.buf[(L.cur + s + 1) & 1];
+    tile_f32<LD>(fin, fout, with_shape(qs, L), L.t, local);
+}
+
+// Resident blocks per SM requested from the compiler for a tile height of TZ threads
+// (keeps the float-float tile near 96 registers).
+template <int TZ>
+constexpr int ens_min_blocks() { return TZ == 64 ? 10 : TZ == 128 ? 5 : 2; }
+
+template <class P, int TZ>
+__global__ void __launch_bounds__(TZ, ens_min_blocks<TZ>())
+k_ens_step(const EnsLattice* __restrict__ lats, int n, P q, int s) {
+    __shared__ int sbase[Q];
+    const int b = blockIdx.x;
+    const int i = ens_find(lats, n, b);
+    const EnsLattice L = lats[i];
+    ens_tile<LoadNC>(L, b - L.tile_begin, s, q, sbase);
+}
+
+// Spin until *ctr >= need (acquire), the error word is set, or the cycle budget runs out
+// (then the error word gets bit 0).  Returns true when the count was reached.
+__device__ __forceinline__ bool ens_wait(const unsigned int* ctr, unsigned int need, unsigned int* err,
+                                         long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= need) return true;
+        if (*(volatile unsigned int*)err) return false;
+        if (clock64() - t0 > limit) {
+            atomicOr(err, 1u);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// extra_wait > 0 raises every barrier target so that it can never be met (a test of the
+// bounded wait: the launch must end with the error word set, not hang).
+template <class P, int TZ>
+__global__ void __launch_bounds__(TZ, ens_min_blocks<TZ>())
+k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_tiles,
+                 EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
+    __shared__ int sbase[Q];
+    __shared__ unsigned int s_item;
+    __shared__ int s_ok;
+    const unsigned int total = (unsigned int)nsteps * (unsigned int)total_tiles;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned int it = atomicAdd(&ctl->queue, 1u);
+            int ok = 1;
+            if (it < total) {
+                const int s = (int)(it / (unsigned int)total_tiles);
+                const int b = (int)(it % (unsigned int)total_tiles);
+                const int i = ens_find(lats, n, b);
+                if (s > 0 || extra_wait)
+                    ok = ens_wait(&done[i], (unsigned int)s * (unsigned int)lats[i].ntiles + extra_wait,
+                                  &ctl->err, spin_limit);
+            }
+            s_item = it;
+            s_ok = ok;
+        }
+        __syncthreads();
+        const unsigned int it = s_item;
+        if (it >= total || !s_ok) break;
+        const int s = (int)(it / (unsigned int)total_tiles);
+        const int b = (int)(it % (unsigned int)total_tiles);
+        const int i = ens_find(lats, n, b);
+        const EnsLattice L = lats[i];
+        ens_tile<LoadCG>(L, b - L.tile_begin, s, q, sbase);
+        __syncthreads();   // all stores of the tile issued; s_item / sbase may be reused
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[i], 1u);
+        }
+    }
+}
+
+}  // namespace lbm

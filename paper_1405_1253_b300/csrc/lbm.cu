@@ -20,6 +20,7 @@
 #include "step_f32.cuh"
 #include "init_diag.cuh"
 #include "adjoint.cuh"
+#include "ensemble.cuh"
 
 using namespace lbm;
 
@@ -592,6 +593,292 @@ int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, d
     CU(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < d->n_modes; k++) { dA_lo[k] = h[k]; dA_hi[k] = h[d->n_modes + k]; }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Ensembles of lattices (lbm_ensemble_*)
+// ---------------------------------------------------------------------------------
+struct lbm_ensemble {
+    int n = 0, prec = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<lbm_ctx*> ctx;
+    std::vector<EnsLattice> h_lats;
+    EnsLattice* d_lats = nullptr;
+    int total_tiles = 0;
+    EnsControl* d_ctl = nullptr;
+    unsigned int* d_done = nullptr;
+    int mode = 1;            // 0: one launch per step, 1: one persistent launch
+    int tz = 128;            // tile height (threads per CTA)
+    int ctas_per_sm = 0;     // persistent grid: CTAs per SM (0: as many as fit)
+    long long spin_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
+    unsigned int extra_wait = 0;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int> g_cur;
+    int g_steps = 0;
+};
+
+static int ens_layout(lbm_ensemble* e) {
+    e->h_lats.resize(e->n);
+    int tb = 0;
+    for (int i = 0; i < e->n; i++) {
+        lbm_ctx* c = e->ctx[i];
+        EnsLattice& L = e->h_lats[i];
+        L.buf[0] = c->buf[0];
+        L.buf[1] = c->buf[1];
+        L.Lx = c->Lx; L.Lz = c->Lz; L.plane = c->Lx * c->Lz;
+        L.cur = c->cur;
+        L.t = make_tiling(c->Lx, c->Lz, e->tz);
+        L.tile_begin = tb;
+        L.ntiles = tiling_blocks(L.t, c->Lx);
+        tb += L.ntiles;
+    }
+    e->total_tiles = tb;
+    // stream-ordered: kernels of an earlier call on the same stream still read the old table
+    // (a pageable source is staged before the call returns, so h_lats may change afterwards)
+    CU(cudaMemcpyAsync(e->d_lats, e->h_lats.data(), e->n * sizeof(EnsLattice), cudaMemcpyHostToDevice,
+                       e->stream));
+    return LBM_OK;
+}
+
+template <class P, int TZ>
+static int ens_launch_tz(lbm_ensemble* e, const P& q, int nsteps) {
+    if (e->mode == 0) {
+        for (int s = 0; s < nsteps; s++) {
+            k_ens_step<P, TZ><<<e->total_tiles, TZ, 0, e->stream>>>(e->d_lats, e->n, q, s);
+            LAUNCH_CHECK();
+        }
+        return LBM_OK;
+    }
+    if ((long long)nsteps * e->total_tiles >= (1LL << 32)) return fail(LBM_EINVAL, "too many work items for one launch");
+    int per_sm = 0, nsm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<P, TZ>, TZ, 0));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->device));
+    if (per_sm < 1) return fail(LBM_ECUDA, "persistent ensemble kernel does not fit on an SM");
+    if (e->ctas_per_sm > 0) per_sm = std::min(per_sm, e->ctas_per_sm);
+    CU(cudaMemsetAsync(e->d_ctl, 0, sizeof(EnsControl), e->stream));
+    CU(cudaMemsetAsync(e->d_done, 0, e->n * sizeof(unsigned int), e->stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(per_sm * nsm);
+    cfg.blockDim = dim3(TZ);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = e->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CU(cudaLaunchKernelEx(&cfg, k_ens_persistent<P, TZ>, (const EnsLattice*)e->d_lats, e->n, q, nsteps,
+                          e->total_tiles, e->d_ctl, e->d_done, e->spin_limit, e->extra_wait));
+    return LBM_OK;
+}
+
+static int ens_launch(lbm_ensemble* e, int nsteps) {
+    lbm_ctx* c0 = e->ctx[0];
+    const StepParams p = step_params(c0);
+    if (e->prec == LBM_F64_FF) {
+        const StepParamsFF q = ff_params(p);
+        switch (e->tz) {
+            case 64: return ens_launch_tz<StepParamsFF, 64>(e, q, nsteps);
+            case 128: return ens_launch_tz<StepParamsFF, 128>(e, q, nsteps);
+            default: return ens_launch_tz<StepParamsFF, 256>(e, q, nsteps);
+        }
+    }
+    const StepParamsF q = f32_params(p);
+    switch (e->tz) {
+        case 64: return ens_launch_tz<StepParamsF, 64>(e, q, nsteps);
+        case 128: return ens_launch_tz<StepParamsF, 128>(e, q, nsteps);
+        default: return ens_launch_tz<StepParamsF, 256>(e, q, nsteps);
+    }
+}
+
+static void ens_drop_graph(lbm_ensemble* e) {
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+    e->g_steps = 0;
+}
+
+extern "C" {
+
+int lbm_ensemble_create(lbm_ensemble** out, int n, lbm_ctx* const* ctxs) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !ctxs) return fail(LBM_EINVAL, "need n >= 1 contexts");
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i]) return fail(LBM_EINVAL, "context %d is NULL", i);
+        const lbm_ctx* a = ctxs[0];
+        const lbm_ctx* b = ctxs[i];
+        if (b->device != a->device || b->prec != a->prec || b->tau != a->tau || b->grav != a->grav ||
+            b->stream != a->stream)
+            return fail(LBM_EINVAL, "context %d differs from context 0 in device, precision, tau, g or stream", i);
+    }
+    if (ctxs[0]->prec != LBM_F64_FF && ctxs[0]->prec != LBM_F32)
+        return fail(LBM_EINVAL, "ensembles take LBM_F64_FF or LBM_F32 contexts");
+    DeviceGuard dg(ctxs[0]->device);
+    lbm_ensemble* e = new lbm_ensemble();
+    e->n = n;
+    e->prec = ctxs[0]->prec;
+    e->device = ctxs[0]->device;
+    e->stream = ctxs[0]->stream;
+    e->ctx.assign(ctxs, ctxs + n);
+    bool ok = cudaMalloc(&e->d_lats, n * sizeof(EnsLattice)) == cudaSuccess &&
+              cudaMalloc(&e->d_ctl, sizeof(EnsControl)) == cudaSuccess &&
+              cudaMalloc(&e->d_done, n * sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) {
+        cudaFree(e->d_lats); cudaFree(e->d_ctl); cudaFree(e->d_done);
+        delete e;
+        return fail(LBM_ENOMEM, "ensemble control allocation failed");
+    }
+    cudaMemset(e->d_ctl, 0, sizeof(EnsControl));
+    *out = e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_destroy(lbm_ensemble* e) {
+    if (!e) return LBM_OK;
+    DeviceGuard dg(e->device);
+    cudaStreamSynchronize(e->stream);
+    ens_drop_graph(e);
+    cudaFree(e->d_lats); cudaFree(e->d_ctl); cudaFree(e->d_done);
+    delete e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_config(lbm_ensemble* e, int mode, int tile_z, int ctas_per_sm) {
+    if (!e) return fail(LBM_EINVAL, "ensemble is NULL");
+    if (mode != 0 && mode != 1) return fail(LBM_EINVAL, "mode must be 0 (per step) or 1 (persistent)");
+    if (tile_z != 64 && tile_z != 128 && tile_z != 256) return fail(LBM_EINVAL, "tile_z must be 64, 128 or 256");
+    if (ctas_per_sm < 0) return fail(LBM_EINVAL, "ctas_per_sm < 0");
+    e->mode = mode;
+    e->tz = tile_z;
+    e->ctas_per_sm = ctas_per_sm;
+    ens_drop_graph(e);
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_wait(lbm_ensemble* e, long long spin_limit_cycles, unsigned int extra_wait) {
+    if (!e || spin_limit_cycles < 1) return fail(LBM_EINVAL, "bad arguments");
+    e->spin_limit = spin_limit_cycles;
+    e->extra_wait = extra_wait;
+    ens_drop_graph(e);
+    return LBM_OK;
+}
+
+int lbm_ensemble_step(lbm_ensemble* e, int nsteps) {
+    if (!e) return fail(LBM_EINVAL, "ensemble is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    DeviceGuard dg(e->device);
+    int rc = ens_layout(e);
+    if (rc) return rc;
+    rc = ens_launch(e, nsteps);
+    if (rc) return rc;
+    for (lbm_ctx* c : e->ctx) c->cur ^= (nsteps & 1);
+    return LBM_OK;
+}
+
+int lbm_ensemble_sync(lbm_ensemble* e) {
+    if (!e) return fail(LBM_EINVAL, "ensemble is NULL");
+    DeviceGuard dg(e->device);
+    CU(cudaStreamSynchronize(e->stream));
+    EnsControl h;
+    CU(cudaMemcpy(&h, e->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+    if (h.err) {
+        CU(cudaMemset(e->d_ctl, 0, sizeof h));
+        return fail(LBM_ETIMEOUT, "persistent ensemble: a step barrier wait ran out (error word 0x%x)", h.err);
+    }
+    return LBM_OK;
+}
+
+int lbm_ensemble_capture(lbm_ensemble* e, int nsteps) {
+    if (!e) return fail(LBM_EINVAL, "ensemble is NULL");
+    if (nsteps < 1) return fail(LBM_EINVAL, "nsteps < 1");
+    DeviceGuard dg(e->device);
+    ens_drop_graph(e);
+    int rc = ens_layout(e);
+    if (rc) return rc;
+    if (!e->stream) return fail(LBM_EINVAL, "graph capture needs a non-default stream");
+    CU(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    rc = ens_launch(e, nsteps);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(LBM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&e->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+        e->gexec = nullptr;
+        return fail(LBM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    e->g_steps = nsteps;
+    e->g_cur.clear();
+    for (lbm_ctx* c : e->ctx) e->g_cur.push_back(c->cur);
+    return LBM_OK;
+}
+
+int lbm_ensemble_graph_launch(lbm_ensemble* e) {
+    if (!e || !e->gexec) return fail(LBM_ESTATE, "no captured graph");
+    for (int i = 0; i < e->n; i++)
+        if (e->ctx[i]->cur != e->g_cur[i])
+            return fail(LBM_ESTATE, "lattice %d is not in the buffer the graph was captured for", i);
+    DeviceGuard dg(e->device);
+    CU(cudaGraphLaunch(e->gexec, e->stream));
+    for (int i = 0; i < e->n; i++) e->ctx[i]->cur ^= (e->g_steps & 1);
+    return LBM_OK;
+}
+
+int lbm_ensemble_tune(lbm_ensemble* e, int steps, double* best_ms, int* best_mode, int* best_tz, int* best_ctas) {
+    if (!e || steps < 1) return fail(LBM_EINVAL, "bad arguments");
+    DeviceGuard dg(e->device);
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    double best = 1e300;
+    int bm = 1, bt = 128, bc = 0;
+    const int tzs[3] = {64, 128, 256};
+    for (int mode = 0; mode <= 1; mode++)
+        for (int ti = 0; ti < 3; ti++)
+            for (int ctas = (mode ? 1 : 0); ctas <= (mode ? 10 : 0); ctas++) {
+                e->mode = mode; e->tz = tzs[ti]; e->ctas_per_sm = ctas;
+                if (mode) {   // skip CTA counts beyond what fits
+                    int per_sm = 0;
+                    cudaError_t oe = (e->prec == LBM_F64_FF)
+                        ? (tzs[ti] == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsFF, 64>, 64, 0)
+                           : tzs[ti] == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsFF, 128>, 128, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsFF, 256>, 256, 0))
+                        : (tzs[ti] == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsF, 64>, 64, 0)
+                           : tzs[ti] == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsF, 128>, 128, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<StepParamsF, 256>, 256, 0));
+                    if (oe != cudaSuccess) return fail(LBM_ECUDA, "occupancy query failed");
+                    if (ctas > per_sm) continue;
+                }
+                int rc = lbm_ensemble_step(e, steps);          // warm
+                if (!rc) rc = lbm_ensemble_sync(e);
+                if (rc) return rc;
+                CU(cudaEventRecord(a, e->stream));
+                rc = lbm_ensemble_step(e, steps);
+                if (rc) return rc;
+                CU(cudaEventRecord(b, e->stream));
+                CU(cudaEventSynchronize(b));
+                rc = lbm_ensemble_sync(e);
+                if (rc) return rc;
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) { best = ms; bm = mode; bt = tzs[ti]; bc = ctas; }
+            }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->mode = bm; e->tz = bt; e->ctas_per_sm = bc;
+    ens_drop_graph(e);
+    if (best_ms) *best_ms = best / steps;
+    if (best_mode) *best_mode = bm;
+    if (best_tz) *best_tz = bt;
+    if (best_ctas) *best_ctas = bc;
     return LBM_OK;
 }
 

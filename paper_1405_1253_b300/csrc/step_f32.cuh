@@ -83,32 +83,43 @@ __device__ __forceinline__ void collide_f32(const float (&g)[Q], float (&fo)[Q],
     });
 }
 
-template <bool WALL>
+template <bool WALL, class LD>
 __device__ __forceinline__ void site_f32(const float* __restrict__ fin, float* __restrict__ fout,
                                         const SiteAddr& ad, const StepParamsF& p) {
     float g[Q], fo[Q];
-    static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + ad.template src<decltype(l)::value, WALL>()); });
+    static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
     collide_f32(g, fo, p);
     const int o = ad.dst();
 #pragma unroll
     for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
 }
 
-__global__ void __launch_bounds__(BLOCK_Z)
-k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
+template <class LD>
+__device__ __forceinline__ void tile_f32(const float* __restrict__ fin, float* __restrict__ fout,
+                                        const StepParamsF& p, Tiling t, int b) {
     SiteAddr ad;
     bool wall;
-    if (!ad.setup(p.Lx, p.Lz, p.plane, t, wall)) return;
-    if (wall) site_f32<true>(fin, fout, ad, p);
-    else site_f32<false>(fin, fout, ad, p);
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+    if (wall) site_f32<true, LD>(fin, fout, ad, p);
+    else site_f32<false, LD>(fin, fout, ad, p);
 }
 
-inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, cudaStream_t st) {
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
+    tile_f32<LoadNC>(fin, fout, p, t, blockIdx.x);
+}
+
+inline StepParamsF f32_params(const StepParams& p) {
     StepParamsF q;
     q.Lx = p.Lx; q.Lz = p.Lz; q.plane = p.plane;
     q.omega = (float)p.omega;
     q.us_z = (float)p.us_z;
     q.T_shift = (float)p.T_shift;
+    return q;
+}
+
+inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, cudaStream_t st) {
+    const StepParamsF q = f32_params(p);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     k_step_f32<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }

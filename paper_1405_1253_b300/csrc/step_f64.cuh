@@ -78,24 +78,31 @@ __device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q
     });
 }
 
-template <bool WALL>
+template <bool WALL, class LD>
 __device__ __forceinline__ void site_f64(const double* __restrict__ fin, double* __restrict__ fout,
                                         const SiteAddr& ad, const StepParams& p) {
     double g[Q], fo[Q];
-    static_for<Q>([&](auto l) { g[l.value] = __ldg(fin + ad.template src<decltype(l)::value, WALL>()); });
+    static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
     collide_f64(g, fo, p);
     const int o = ad.dst();
 #pragma unroll
     for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
 }
 
-__global__ void __launch_bounds__(BLOCK_Z)
-k_step_f64(const double* __restrict__ fin, double* __restrict__ fout, StepParams p, Tiling t) {
+// One BLOCK_Z-thread tile b of the lattice tiling t.
+template <class LD>
+__device__ __forceinline__ void tile_f64(const double* __restrict__ fin, double* __restrict__ fout,
+                                        const StepParams& p, Tiling t, int b) {
     SiteAddr ad;
     bool wall;
-    if (!ad.setup(p.Lx, p.Lz, p.plane, t, wall)) return;
-    if (wall) site_f64<true>(fin, fout, ad, p);
-    else site_f64<false>(fin, fout, ad, p);
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+    if (wall) site_f64<true, LD>(fin, fout, ad, p);
+    else site_f64<false, LD>(fin, fout, ad, p);
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f64(const double* __restrict__ fin, double* __restrict__ fout, StepParams p, Tiling t) {
+    tile_f64<LoadNC>(fin, fout, p, t, blockIdx.x);
 }
 
 inline void launch_step_f64(const double* fin, double* fout, const StepParams& p, cudaStream_t st) {

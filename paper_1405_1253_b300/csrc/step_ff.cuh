@@ -31,21 +31,13 @@ __device__ __forceinline__ ff dsplit(double x) {
     return bits_to_ff((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x));
 }
 
-// Second read of a population already read in the moment pass (served by L1/L2): issued
-// as its own instruction so the first copy need not stay live in registers.
-__device__ __forceinline__ double ld_again(const double* ptr) {
-    double v;
-    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(ptr));
-    return v;
-}
-
 template <bool WALL>
 __device__ __forceinline__ int pull_src(const SiteAddr& ad, const int* sbase, int l, int lop, int vx, int vz) {
     if constexpr (WALL) return ad.template src_rt<true>(l, lop, vx, vz);
     else return sbase[l] + ad.z;
 }
 
-template <bool WALL>
+template <bool WALL, class LD>
 __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* __restrict__ fout,
                                        const SiteAddr& ad, const int* sbase, const StepParamsFF& p) {
     // -- pass 1: exact moments in 64-bit fixed point (all 37 loads in flight) -----------
@@ -57,13 +49,13 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     int64_t R, Jx = 0, Jz = 0, E = 0;
     int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
     {
-        const double v0 = __ldg(fin + src1(Tag<0>{}));
+        const double v0 = LD::ld(fin + src1(Tag<0>{}));
         R = bits_to_fix60((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
     }
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        const double va = __ldg(fin + src1(Tag<A>{}));
-        const double vb = __ldg(fin + src1(Tag<B>{}));
+        const double va = LD::ld(fin + src1(Tag<A>{}));
+        const double vb = LD::ld(fin + src1(Tag<B>{}));
         const int64_t fa = bits_to_fix60((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
         const int64_t fb = bits_to_fix60((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
         const int64_t ps = fa + fb, ms = fa - fb;
@@ -107,7 +99,7 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     // -- pass 2: relaxation; rolled loops over shells and their pairs keep the code in
     //    the instruction cache, the shell coefficients are formed once per shell -------
     {
-        const double v0 = ld_again(fin + src1(Tag<0>{}));
+        const double v0 = LD::ld_again(fin + src1(Tag<0>{}));
         const ff W0 = ff_mul(orho, ff_make(d_lat.wf_hi[0], d_lat.wf_lo[0]));
         fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
     }
@@ -117,13 +109,13 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     ff K0, K1, K2, W;
     int sh_cur = 0;
     PairInfo pi = d_pairs[0];
-    double va = ld_again(fin + pull_src<WALL>(ad, sbase, pi.A, pi.B, pi.cx, pi.cz));
-    double vb = ld_again(fin + pull_src<WALL>(ad, sbase, pi.B, pi.A, -pi.cx, -pi.cz));
+    double va = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pi.A, pi.B, pi.cx, pi.cz));
+    double vb = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pi.B, pi.A, -pi.cx, -pi.cz));
 #pragma unroll 1
     for (int k = 0; k < NPAIR; k++) {
         const PairInfo pn = d_pairs[k + 1 < NPAIR ? k + 1 : k];
-        const double va_n = ld_again(fin + pull_src<WALL>(ad, sbase, pn.A, pn.B, pn.cx, pn.cz));
-        const double vb_n = ld_again(fin + pull_src<WALL>(ad, sbase, pn.B, pn.A, -pn.cx, -pn.cz));
+        const double va_n = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pn.A, pn.B, pn.cx, pn.cz));
+        const double vb_n = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pn.B, pn.A, -pn.cx, -pn.cz));
         if (pi.shell != sh_cur) {
             sh_cur = pi.shell;
             const float C2 = pi.fc2;
@@ -152,19 +144,27 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     }
 }
 
-__global__ void __launch_bounds__(BLOCK_Z, 5)
-k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
-    __shared__ int sbase[Q];
-    const bool wall_tile = tile_is_wall(t);
+// One tile b of the lattice tiling t; sbase: Q ints of shared memory.  All threads of the
+// block must call this (it synchronises once after filling sbase).
+template <class LD>
+__device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
+                                       const StepParamsFF& p, Tiling t, int b, int* sbase) {
+    const bool wall_tile = tile_is_wall(t, b);
     if (!wall_tile) {
-        fill_pull_bases(sbase, tile_column(t), p.Lx, p.Lz, p.plane);
+        fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
         __syncthreads();
     }
     SiteAddr ad;
     bool wall;
-    if (!ad.setup(p.Lx, p.Lz, p.plane, t, wall)) return;
-    if (wall) site_ff<true>(fin, fout, ad, sbase, p);
-    else site_ff<false>(fin, fout, ad, sbase, p);
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+    if (wall) site_ff<true, LD>(fin, fout, ad, sbase, p);
+    else site_ff<false, LD>(fin, fout, ad, sbase, p);
+}
+
+__global__ void __launch_bounds__(BLOCK_Z, 5)
+k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
+    __shared__ int sbase[Q];
+    tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
 }
 
 inline ff ff_host(double v) {
@@ -174,7 +174,7 @@ inline ff ff_host(double v) {
     return r;
 }
 
-inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, cudaStream_t st) {
+inline StepParamsFF ff_params(const StepParams& p) {
     StepParamsFF q;
     q.Lx = p.Lx; q.Lz = p.Lz; q.plane = p.plane;
     q.omega = p.omega;
@@ -183,6 +183,11 @@ inline void launch_step_ff(const double* fin, double* fout, const StepParams& p,
     q.one_m_omega_d = p.one_m_omega;
     q.c24 = ff_host(1.0 / 24.0);
     q.c6 = ff_host(1.0 / 6.0);
+    return q;
+}
+
+inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, cudaStream_t st) {
+    const StepParamsFF q = ff_params(p);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     k_step_ff<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }

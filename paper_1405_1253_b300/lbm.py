@@ -54,6 +54,15 @@ _SIGS = {
     "lbm_sync": (_i, [_vp]),
     "lbm_lattice": (_i, [_ip, _dp, _dp]),
     "lbm_row_mean_T_noalloc": (_i, [_vp, _i, _i, _vp, _vp]),
+    "lbm_ensemble_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "lbm_ensemble_destroy": (_i, [_vp]),
+    "lbm_ensemble_config": (_i, [_vp, _i, _i, _i]),
+    "lbm_ensemble_tune": (_i, [_vp, _i, _dp, _ip, _ip, _ip]),
+    "lbm_ensemble_step": (_i, [_vp, _i]),
+    "lbm_ensemble_capture": (_i, [_vp, _i]),
+    "lbm_ensemble_graph_launch": (_i, [_vp]),
+    "lbm_ensemble_sync": (_i, [_vp]),
+    "lbm_ensemble_set_wait": (_i, [_vp, ctypes.c_longlong, ctypes.c_uint]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -224,3 +233,52 @@ class Lattice:
         dlo, dhi = np.zeros(max(K, 1)), np.zeros(max(K, 1))
         _check(_lib.lbm_init_adjoint(self.ctx, ctypes.byref(d), lam0.data_ptr(), _dptr(dlo), _dptr(dhi)))
         return dlo[:K], dhi[:K]
+
+
+class Ensemble:
+    """Independent lattices advanced together (one launch per step, or one persistent
+    launch under an optional CUDA graph).  `lattices` are Lattice objects sharing the
+    device, precision ("f64_ff" or "f32"), tau, g and stream."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        arr = (_vp * len(self.lattices))(*[L.ctx for L in self.lattices])
+        e = _vp()
+        _check(_lib.lbm_ensemble_create(ctypes.byref(e), len(self.lattices), arr))
+        self.e = e
+
+    def config(self, mode: int = 1, tile_z: int = 128, ctas_per_sm: int = 0):
+        _check(_lib.lbm_ensemble_config(self.e, int(mode), int(tile_z), int(ctas_per_sm)))
+
+    def tune(self, steps: int = 5):
+        ms = ctypes.c_double()
+        mode, tz, ctas = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.lbm_ensemble_tune(self.e, int(steps), ctypes.byref(ms), ctypes.byref(mode),
+                                      ctypes.byref(tz), ctypes.byref(ctas)))
+        return {"ms_per_step": ms.value, "mode": mode.value, "tile_z": tz.value, "ctas_per_sm": ctas.value}
+
+    def step(self, n: int = 1):
+        _check(_lib.lbm_ensemble_step(self.e, int(n)))
+
+    def capture(self, n: int):
+        _check(_lib.lbm_ensemble_capture(self.e, int(n)))
+
+    def graph_launch(self):
+        _check(_lib.lbm_ensemble_graph_launch(self.e))
+
+    def sync(self):
+        _check(_lib.lbm_ensemble_sync(self.e))
+
+    def set_wait(self, spin_limit_cycles: int, extra_wait: int = 0):
+        _check(_lib.lbm_ensemble_set_wait(self.e, int(spin_limit_cycles), int(extra_wait)))
+
+    def close(self):
+        if getattr(self, "e", None):
+            _lib.lbm_ensemble_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
