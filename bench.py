@@ -34,7 +34,7 @@ from paper_1405_1253_b300 import workloads as W  # noqa: E402
 Q = 37
 METRIC = "MLUPS and % HBM roofline, FP64 vs FP32-storage (stated error), adjoint/forward"
 BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4}
-ARITH = {"f64": "f64", "f64_ff": "f32x2", "f32": "f32"}
+ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32"}
 KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32"}
 
 
@@ -194,6 +194,84 @@ def time_variant(torch, lbm, lat, prec, steps, warmup, stream):
     return ms
 
 
+def bench_ensemble(torch, lbm, prec, steps, stream):
+    """The 48-lattice ensemble (16 x 256x512, 16 x 512x1024, 16 x 384x1536): autotuned,
+    captured once as a CUDA graph of `steps` steps, replayed and timed."""
+    lats = W.ensemble_48()
+    Ls = []
+    for lat in lats:
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        Ls.append(L)
+    ens = lbm.Ensemble(Ls)
+    tuned = ens.tune(steps=2)
+    for L, lat in zip(Ls, lats):        # the trials advanced the state: start again
+        L.init_from(lat)
+    ens.capture(steps)
+    ens.graph_launch()                  # warm-up replay
+    ens.sync()
+    for L, lat in zip(Ls, lats):
+        L.init_from(lat)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.graph_launch()
+    e1.record(stream)
+    e1.synchronize()
+    ens.sync()
+    ms = e0.elapsed_time(e1)
+    sites = sum(l.sites for l in lats)
+    mass = Ls[0].global_sums()[0]
+    ens.close()
+    for L in Ls:
+        L.close()
+    bps = 2 * Q * BYTES_PER_POP[prec]
+    return {"lattices": len(lats), "sites": sites, "steps": steps, "ms_per_step": ms / steps,
+            "mlups": sites * steps / (ms * 1e-3) / 1e6, "gbs": bps * sites * steps / (ms * 1e-3) / 1e9,
+            "tuned": tuned, "finite": bool(np.isfinite(mass)), "launch": "one persistent launch" if tuned["mode"] == 1
+            else "one launch per step", "graph": "one CUDA graph replay"}
+
+
+def bench_adjoint(torch):
+    """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and
+    backward (recompute + adjoint) wall times and device memory."""
+    from paper_1405_1253_b300 import adjoint
+    lat = W.GRADIENT_256x512
+    drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT)
+    m = lat.modes()
+    drv.forward(m.amp_lo, m.amp_hi)      # warm
+    drv.backward()
+    drv.forward(m.amp_lo, m.amp_hi)
+    g_lo, g_hi = drv.backward()
+    st = drv.stats
+    drv.close()
+    return {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (FP64)",
+            "forward_s": st.forward_s, "backward_s": st.backward_s, "backward_over_forward": st.backward_s / st.forward_s,
+            "memory_bytes": st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes,
+            "forward_memory_bytes": 2 * st.state_bytes,
+            "memory_over_forward": (st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes) / (2 * st.state_bytes),
+            "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
+
+
+def fp32_error(torch, lbm, lat, steps, stream):
+    """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
+    step after `steps` steps from the same initial state."""
+    out = {}
+    fields = {}
+    for prec in ("f64_ff", "f32"):
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        L.step(steps)
+        rho, _, _, T = L.moments()
+        fields[prec] = (rho, T, L.widths(lat.T_u, lat.T_m, lat.T_d))
+        L.close()
+    (r64, T64, w64), (r32, T32, w32) = fields["f64_ff"], fields["f32"]
+    out["steps"] = steps
+    out["rho_rel_l2"] = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
+    out["T_rel_l2"] = float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64))
+    out["width_rel_err"] = [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_setup()
@@ -259,6 +337,14 @@ def run_ours(args):
             variants[v] = {"mlups": sites / (vms * 1e-3) / 1e6, "ms_per_step": vms,
                            "gbs": vbytes / (vms * 1e-3) / 1e9, "arith": ARITH[v]}
 
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["fp32_error_1024x2048"] = fp32_error(torch, lbm, lat, 500, stream)
+        es = torch.cuda.Stream()           # graph capture needs a non-default stream
+        extras["ensemble_f64"] = bench_ensemble(torch, lbm, "f64_ff", 100, es)
+        extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", 100, es)
+        extras["adjoint"] = bench_adjoint(torch)
+
     if rank != 0:
         return
     peaks, peak_kind = measured_peaks()
@@ -294,6 +380,7 @@ def run_ours(args):
         "mass_after": mass,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -308,6 +395,7 @@ def main():
     ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip ensemble, adjoint and FP32-error sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
