@@ -123,6 +123,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(ms_total: float, steps: int, sites_per_rank: int, world_size: int, device=None):
+    """Whole-job figures from one rank's timed region: the slowest rank's time (max over
+    ranks, a collective when world_size > 1) and the aggregate MLUPS of all ranks'
+    independent lattices.  Returns (ms_total_max, ms_per_step, mlups)."""
+    if world_size > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / steps
+    return ms_total, ms_step, world_size * sites_per_rank / (ms_step * 1e-3) / 1e6
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -302,13 +316,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms_total = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    mlups = ws * sites / (ms_step * 1e-3) / 1e6
+    ms_total, ms_step, mlups = aggregate_ranks(e0.elapsed_time(e1), args.steps, sites, ws, device="cuda")
     mass = L.global_sums()[0]
 
     # end to end through the C ABI with host buffers: host -> device state, one step,

@@ -1,0 +1,51 @@
+"""The N > 1 host logic of bench.py on CPU ranks (gloo, world size 2): the timed region is
+the slowest rank's, and the aggregate rate counts every rank's replica."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms_local = [100.0, 250.0][rank]
+    res = bench.aggregate_ranks(ms_local, steps=50, sites_per_rank=1000, world_size=world, device="cpu")
+    q.put((rank, res))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in (0, 1):
+        ms_total, ms_step, mlups = out[rank]
+        assert ms_total == 250.0                      # max over ranks
+        assert ms_step == 5.0
+        assert mlups == pytest.approx(2 * 1000 / 5e-3 / 1e6)
+
+
+def test_single_rank_needs_no_collective():
+    import bench
+    assert bench.aggregate_ranks(80.0, 40, 2000, 1) == (80.0, 2.0, 2000 / 2e-3 / 1e6)
