@@ -41,6 +41,12 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 
+// General sum, not renormalised (|lo| stays within a few ulps of hi).
+__device__ __forceinline__ ff ff_add_u(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return ff{s.hi, s.lo + (a.lo + b.lo)};
+}
+
 // Sum when |a| >= |b| is known, not renormalised.
 __device__ __forceinline__ ff ff_add_big_u(ff a, ff b) {
     const float s = a.hi + b.hi;
@@ -112,7 +118,9 @@ __device__ __forceinline__ int64_t bits_to_fix60(uint32_t H, uint32_t L) {
     return (H & 0x80000000u) ? -v : v;
 }
 
-// Normalised float-float (|lo| <= ulp(hi)/2) -> binary64, rounded to nearest.
+
+// Normalised float-float (|lo| <= ulp(hi)/2, hi a normal FP32 number) -> binary64,
+// rounded to nearest.
 // The pattern of (double)hi is built from the FP32 fields; lo is added as an integer
 // count of binary64 ulps of hi's binade (halved ulps when the sum drops below a power of two).
 __device__ __forceinline__ double ff_to_double_bits(ff a) {
@@ -128,9 +136,7 @@ __device__ __forceinline__ double ff_to_double_bits(ff a) {
         sbits += (1u << 23);
     const int32_t k = __float2int_rn(a.lo * __uint_as_float(sbits));
     const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (uint64_t)(int64_t)k;
-    const uint32_t outH = ha >= 0x00800000u ? ((uint32_t)(P >> 32) | sgn) : 0u;
-    const uint32_t outL = ha >= 0x00800000u ? (uint32_t)P : 0u;
-    return __hiloint2double((int)outH, (int)outL);
+    return __hiloint2double((int)((uint32_t)(P >> 32) | sgn), (int)(uint32_t)P);
 }
 
 }  // namespace lbm

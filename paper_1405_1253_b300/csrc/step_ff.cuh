@@ -46,8 +46,10 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         if constexpr (WALL) return ad.template src<L, true>();
         else return sbase[L] + ad.z;
     };
-    int64_t R, Jx = 0, Jz = 0, E = 0;
+    // pair sums by shell, pair differences grouped by |c_x| and |c_z| (no multiplies)
+    int64_t R, Jx, Jz, E = 0;
     int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t GX[4] = {0, 0, 0, 0}, GZ[4] = {0, 0, 0, 0};
     {
         const double v0 = LD::ld(fin + src1(Tag<0>{}));
         R = bits_to_fix60((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
@@ -58,10 +60,12 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const double vb = LD::ld(fin + src1(Tag<B>{}));
         const int64_t fa = bits_to_fix60((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
         const int64_t fb = bits_to_fix60((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
-        const int64_t ps = fa + fb, ms = fa - fb;
-        S[shell_of(A)] += ps;
-        if constexpr (cx(A) != 0) Jx += (int64_t)cx(A) * ms;
-        if constexpr (cz(A) != 0) Jz += (int64_t)cz(A) * ms;
+        S[shell_of(A)] += fa + fb;
+        constexpr int AX = cx(A) < 0 ? -cx(A) : cx(A), AZ = cz(A) < 0 ? -cz(A) : cz(A);
+        if constexpr (cx(A) > 0) GX[AX] += fa - fb;
+        if constexpr (cx(A) < 0) GX[AX] += fb - fa;
+        if constexpr (cz(A) > 0) GZ[AZ] += fa - fb;
+        if constexpr (cz(A) < 0) GZ[AZ] += fb - fa;
     });
     static_for<NSHELL>([&](auto s) {
         constexpr int SS = decltype(s)::value;
@@ -70,6 +74,8 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
             E += (int64_t)shell_c2(SS) * S[SS];
         }
     });
+    Jx = GX[1] + 2 * GX[2] + 3 * GX[3];
+    Jz = GZ[1] + 2 * GZ[2] + 3 * GZ[3];
     // -- per-site scalars in FP64 (the 2^60 scale cancels in the ratios) -----------------
     const double r = d_lat.r;
     const double rho_i = (double)R;
@@ -103,27 +109,11 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const ff W0 = ff_mul(orho, ff_make(d_lat.wf_hi[0], d_lat.wf_lo[0]));
         fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
     }
-    // Flattened loop over the 18 pairs (grouped by shell); the shell coefficients are
-    // re-formed when the shell changes, and the two populations of the next pair are
-    // requested one iteration ahead so that the reload latency overlaps the arithmetic.
-    ff K0, K1, K2, W;
-    int sh_cur = 0;
-    PairInfo pi = d_pairs[0];
-    double va = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pi.A, pi.B, pi.cx, pi.cz));
-    double vb = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pi.B, pi.A, -pi.cx, -pi.cz));
-#pragma unroll 1
-    for (int k = 0; k < NPAIR; k++) {
-        const PairInfo pn = d_pairs[k + 1 < NPAIR ? k + 1 : k];
-        const double va_n = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pn.A, pn.B, pn.cx, pn.cz));
-        const double vb_n = LD::ld_again(fin + pull_src<WALL>(ad, sbase, pn.B, pn.A, -pn.cx, -pn.cz));
-        if (pi.shell != sh_cur) {
-            sh_cur = pi.shell;
-            const float C2 = pi.fc2;
-            K0 = ff_add(k00, ff_mul_f_u(ff_add(k01, ff_mul_f_u(k02, C2)), C2));
-            K1 = ff_add(k10, ff_mul_f_u(k11, C2));
-            K2 = ff_add(k20, ff_mul_f_u(k21, C2));
-            W = ff_mul(orho, ff_make(d_lat.wf_hi[sh_cur], d_lat.wf_lo[sh_cur]));
-        }
+    // Loop over the shells; each shell (2 or 4 pairs) is processed two pairs at a time, so
+    // two independent dependency chains are in flight per thread.  The shell coefficients
+    // are formed once per shell; loops stay rolled to keep the code in the I-cache.
+    auto pair_out = [&](const PairInfo& pi, const ff& K0, const ff& K1, const ff& K2, const ff& W,
+                        double va, double vb) {
         // s = xi_A . u_s = c_x a + c_z b (left unnormalised)
         const ff sx = ff_mul_f_u(a, pi.fcx), sz = ff_mul_f_u(b, pi.fcz);
         const ff st = two_sum(sx.hi, sz.hi);
@@ -138,9 +128,25 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const double Xm = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, ff_neg(Pb))));
         fout[pi.A * p.plane + o] = fma(p.one_m_omega_d, va, Xp);
         fout[pi.B * p.plane + o] = fma(p.one_m_omega_d, vb, Xm);
-        pi = pn;
-        va = va_n;
-        vb = vb_n;
+    };
+#pragma unroll 1
+    for (int sh = 1; sh < NSHELL; sh++) {
+        const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
+        const float C2 = d_pairs[k0].fc2;
+        const ff K0 = ff_add_u(k00, ff_mul_f_u(ff_add_u(k01, ff_mul_f_u(k02, C2)), C2));
+        const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
+        const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
+        const ff W = ff_mul(orho, ff_make(d_lat.wf_hi[sh], d_lat.wf_lo[sh]));
+#pragma unroll 1
+        for (int k = k0; k < k1; k += 2) {            // every shell has an even number of pairs
+            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
+            const double v0a = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p0.A, p0.B, p0.cx, p0.cz));
+            const double v0b = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p0.B, p0.A, -p0.cx, -p0.cz));
+            const double v1a = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p1.A, p1.B, p1.cx, p1.cz));
+            const double v1b = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p1.B, p1.A, -p1.cx, -p1.cz));
+            pair_out(p0, K0, K1, K2, W, v0a, v0b);
+            pair_out(p1, K0, K1, K2, W, v1a, v1b);
+        }
     }
 }
 
