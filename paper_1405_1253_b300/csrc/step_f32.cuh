@@ -60,27 +60,60 @@ __device__ __forceinline__ void collide_f32(const float (&g)[Q], float (&fo)[Q],
     const float orho = p.omega * rho;
     {
         const float W = orho * d_lat.wf[0];
-        fo[0] = g[0] + (fmaf(W, d00, W) - p.omega * g[0]);
+        fo[0] = fmaf(W, d00, W) - p.omega * g[0];                  // update D_0 (finished below)
     }
+    // Conservation repair.  The update D_l = f'_l - g_l is small, so its moments are summed
+    // accurately in plain FP32; the collide must change them by exactly
+    //   sum D = 0,  sum c D = rho gvec / r,  sum |c|^2 D = rho (2 u.gvec + g^2) / r^2
+    // (mass kept, momentum + rho g, internal energy kept).  FP32 rounding of the weights and
+    // of the equilibrium misses these by ~1e-8 per step, with the same sign across a smooth
+    // region; the residual (d0, d1, d2) is put on the rest and the four |c| = 1 populations:
+    //   rest: d0 - d2;  (+-1, 0): d2/4 +- d1x/2;  (0, +-1): d2/4 +- d1z/2.
+    // All other populations are final as soon as their update is known.
+    float S0 = fo[0], S1x = 0.f, S1z = 0.f, S2 = 0.f;
+    float D1[4];   // updates of the |c| = 1 populations 1..4, finished after the repair
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);
         constexpr int SH = shell_of(A);
         constexpr float C2 = (float)c2(A);
-        const float D0 = fmaf(C2, fmaf(C2, k02, k01), d00);     // K0 - 1
+        const float D0v = fmaf(C2, fmaf(C2, k02, k01), d00);     // K0 - 1
         const float K1 = fmaf(C2, k11, k10);
         const float K2 = fmaf(C2, k21, k20);
-        float s;
-        if constexpr (cx(A) == 0) s = (float)cz(A) * b;
-        else if constexpr (cz(A) == 0) s = (float)cx(A) * a;
-        else s = fmaf((float)cx(A), a, (float)cz(A) * b);
-        const float s2 = s * s;
-        const float Ev = fmaf(s2, fmaf(s2, 1.f / 24.f, K2), D0);  // even part - 1
-        const float Od = s * fmaf(s2, 1.f / 6.f, K1);
+        float sv;
+        if constexpr (cx(A) == 0) sv = (float)cz(A) * b;
+        else if constexpr (cz(A) == 0) sv = (float)cx(A) * a;
+        else sv = fmaf((float)cx(A), a, (float)cz(A) * b);
+        const float s2 = sv * sv;
+        const float Ev = fmaf(s2, fmaf(s2, 1.f / 24.f, K2), D0v);  // even part - 1
+        const float Od = sv * fmaf(s2, 1.f / 6.f, K1);
         const float W = orho * d_lat.wf[SH];
-        // f' = g + (W (1 + Ev +- Od) - omega g)
-        fo[A] = g[A] + (fmaf(W, Ev + Od, W) - p.omega * g[A]);
-        fo[B] = g[B] + (fmaf(W, Ev - Od, W) - p.omega * g[B]);
+        const float Da = fmaf(W, Ev + Od, W) - p.omega * g[A];     // f' = g + (W (1 + Ev +- Od) - w g)
+        const float Db = fmaf(W, Ev - Od, W) - p.omega * g[B];
+        const float sp = Da + Db, dm = Da - Db;
+        S0 += sp;
+        S2 = fmaf(C2, sp, S2);
+        if constexpr (cx(A) != 0) S1x = fmaf((float)cx(A), dm, S1x);
+        if constexpr (cz(A) != 0) S1z = fmaf((float)cz(A), dm, S1z);
+        if constexpr (SH == 1) {
+            D1[A - 1] = Da;
+            D1[B - 1] = Db;
+        } else {
+            fo[A] = g[A] + Da;
+            fo[B] = g[B] + Db;
+        }
     });
+    static_assert(pair_first(0) == 1 && pair_first(1) == 2 && opp(1) == 3 && opp(2) == 4, "shell 1 layout");
+    const float ir = 1.f / r, ir2 = ir * ir;
+    const float gz = p.us_z * p.omega;                             // gvec_z = -g (us_z = -tau g)
+    const float d0 = -S0;
+    const float d1x = -S1x;
+    const float d1z = rho * gz * ir - S1z;
+    const float d2 = rho * (2.f * uz * gz + gz * gz) * ir2 - S2;
+    fo[0] = g[0] + (fo[0] + (d0 - d2));
+    fo[1] = g[1] + (D1[0] + fmaf(0.5f, d1x, 0.25f * d2));
+    fo[3] = g[3] + (D1[2] + fmaf(-0.5f, d1x, 0.25f * d2));
+    fo[2] = g[2] + (D1[1] + fmaf(0.5f, d1z, 0.25f * d2));
+    fo[4] = g[4] + (D1[3] + fmaf(-0.5f, d1z, 0.25f * d2));
 }
 
 template <bool WALL, class LD>
