@@ -35,6 +35,16 @@ __device__ __forceinline__ PDerivs hermite_poly(double s, double C2, double u2, 
     return d;
 }
 
+// Per site, with opposite velocities paired (s -> -s flips the odd parts):
+//   P(s) = E + O,            E = K0 + q (K2 + q/24),  O = s (K1 + q/6),        q = s^2,
+//   dP/ds = E1 + O1,         E1 = K1 + q/2,           O1 = s (2 K2 + q/6),
+//   dP/du2 = G0 - q/4 - s/2, G0 = -1/2 + u2/4 - th (C2 - 4)/4,
+//   dP/dth = H0 + q (C2 - 6)/4 + s (C2 - 4)/2,  H0 = (C2-2)/2 - u2 (C2-4)/4 + th (C2^2-8C2+8)/4,
+// so that with ls = lam_+ + lam_-, ld = lam_+ - lam_-:
+//   A = sum w (ls E + ld O),   B = rho sum w [ xi (ld E1 + ls O1) + 2 u_s (ls (G0 - q/4) - ld s/2) ],
+//   C = rho sum w [ ls (H0 + q (C2-6)/4) + ld s (C2-4)/2 ],
+// and mu_m = (1 - w) lam_m + w (A' + B'.xi_m + C' |xi_m|^2) with
+//   A' = A - B.u/rho + C (|u|^2 - D T)/(D rho),  B' = B/rho - 2 C u/(D rho),  C' = C/(D rho).
 __global__ void __launch_bounds__(BLOCK_Z)
 k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next,
               double* __restrict__ lam_out, StepParams p) {
@@ -44,48 +54,79 @@ k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next
     int col[7];
 #pragma unroll
     for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
-    int src[Q];
     double g[Q];
-    static_for<Q>([&](auto l) {
-        src[l.value] = pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane);
-        g[l.value] = ft[src[l.value]];
+    static_for<Q>([&](auto l) { g[l.value] = ft[pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane)]; });
+    const double r = d_lat.r, r2 = d_lat.r2;
+    double R = g[0], Jx = 0.0, Jz = 0.0, E = 0.0;
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
+        const double ps = g[A_] + g[B_], ms = g[A_] - g[B_];
+        R += ps;
+        if constexpr (cx(A_) != 0) Jx = fma((double)cx(A_), ms, Jx);
+        if constexpr (cz(A_) != 0) Jz = fma((double)cz(A_), ms, Jz);
+        E = fma((double)c2(A_), ps, E);
     });
-    const double r = d_lat.r;
-    double R = 0.0, Jx = 0.0, Jz = 0.0, E = 0.0;
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        R += g[l];
-        Jx += cx(l) * g[l];
-        Jz += cz(l) * g[l];
-        E += c2(l) * g[l];
-    }
-    const double ux = r * Jx / R, uz = r * Jz / R;
-    const double T = 0.5 * (d_lat.r2 * E / R - (ux * ux + uz * uz));
+    const double inv = 1.0 / R;
+    const double ux = r * Jx * inv, uz = r * Jz * inv;
+    const double uu = ux * ux + uz * uz;
+    const double T = 0.5 * (r2 * E * inv - uu);
     const double usx = ux, usz = uz + p.us_z, th = T + p.T_shift - 1.0;
     const double u2 = usx * usx + usz * usz;
+    const double a = r * usx, b = r * usz;          // s_l = c_x a + c_z b
     const int o = x * p.Lz + z;
-    double lam[Q];
-#pragma unroll
-    for (int l = 0; l < Q; l++) lam[l] = lam_next[l * p.plane + o];
-    double A = 0.0, Bx = 0.0, Bz = 0.0, C = 0.0;
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        const double xx = r * cx(l), xz = r * cz(l);
-        const double s = xx * usx + xz * usz;
-        const PDerivs d = hermite_poly(s, d_lat.r2 * c2(l), u2, th);
-        const double w = d_lat.w[shell_of(l)];
-        A += lam[l] * w * d.P;                                     // f^eq / rho
-        Bx += lam[l] * w * R * (d.dPds * xx + 2.0 * d.dPdu2 * usx);
-        Bz += lam[l] * w * R * (d.dPds * xz + 2.0 * d.dPdu2 * usz);
-        C += lam[l] * w * R * d.dPdth;
-    }
-#pragma unroll
-    for (int m = 0; m < Q; m++) {
-        const double dx = r * cx(m) - ux, dz = r * cz(m) - uz;
-        const double mu = p.one_m_omega * lam[m]
-                        + p.omega * (A + (Bx * dx + Bz * dz) / R + C * (dx * dx + dz * dz - DIM * T) / (DIM * R));
-        lam_out[src[m]] = mu;
-    }
+    const double lam0 = lam_next[o];
+    // rest population (s = 0, C2 = 0)
+    double A = d_lat.w[0] * lam0 * (1.0 - 0.5 * u2 - th + 0.125 * u2 * u2 + th * u2 + th * th);
+    double Bx = 0.0, Bz = 0.0, Bu = d_lat.w[0] * lam0 * (-0.5 + 0.25 * u2 + th);
+    double Cs = d_lat.w[0] * lam0 * (-1.0 + u2 + 2.0 * th);
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
+        constexpr int SH = shell_of(A_);
+        const double C2 = r2 * c2(A_);
+        const double K0 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 2.0) + 0.125 * u2 * u2
+                        - 0.25 * th * u2 * (C2 - 4.0) + 0.125 * th * th * (C2 * C2 - 8.0 * C2 + 8.0);
+        const double K1 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 4.0);
+        const double K2 = 0.5 - 0.25 * u2 + 0.25 * th * (C2 - 6.0);
+        double s;
+        if constexpr (cx(A_) == 0) s = (double)cz(A_) * b;
+        else if constexpr (cz(A_) == 0) s = (double)cx(A_) * a;
+        else s = fma((double)cx(A_), a, (double)cz(A_) * b);
+        const double q = s * s;
+        const double Ev = fma(q, fma(q, 1.0 / 24.0, K2), K0);
+        const double Od = s * fma(q, 1.0 / 6.0, K1);
+        const double E1 = fma(q, 0.5, K1);
+        const double O1 = s * fma(q, 1.0 / 6.0, 2.0 * K2);
+        const double G0 = -0.5 + 0.25 * u2 - 0.25 * th * (C2 - 4.0);
+        const double H0 = 0.5 * (C2 - 2.0) - 0.25 * u2 * (C2 - 4.0) + 0.25 * th * (C2 * C2 - 8.0 * C2 + 8.0);
+        const double la = lam_next[A_ * p.plane + o], lb = lam_next[B_ * p.plane + o];
+        const double w = d_lat.w[SH];
+        const double ls = w * (la + lb), ld = w * (la - lb);
+        A = fma(ls, Ev, fma(ld, Od, A));
+        const double bt = fma(ld, E1, ls * O1);          // coefficient of xi_A
+        Bx = fma(r * cx(A_), bt, Bx);
+        Bz = fma(r * cz(A_), bt, Bz);
+        Bu = fma(ls, fma(q, -0.25, G0), fma(ld, -0.5 * s, Bu));
+        Cs = fma(ls, fma(0.25 * (C2 - 6.0), q, H0), fma(ld, 0.5 * (C2 - 4.0) * s, Cs));
+    });
+    // dP/du_s = dP/ds xi + 2 dP/du2 u_s, times rho
+    const double Bxt = R * (Bx + 2.0 * Bu * usx);
+    const double Bzt = R * (Bz + 2.0 * Bu * usz);
+    const double Ct = R * Cs;
+    const double Dr = DIM * R;
+    const double Ap = A - (Bxt * ux + Bzt * uz) * inv + Ct * (uu - DIM * T) / Dr;
+    const double Bpx = Bxt * inv - 2.0 * Ct * ux / Dr;
+    const double Bpz = Bzt * inv - 2.0 * Ct * uz / Dr;
+    const double Cp = Ct / Dr;
+    // scatter mu to the pull sources (unique targets: propagate + bc is a permutation)
+    lam_out[pull_index<0>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, lam0, p.omega * Ap);
+    static_for<NPAIR>([&](auto k) {
+        constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
+        const double ev = fma(Cp, r2 * c2(A_), Ap);
+        const double od = fma(Bpx, r * cx(A_), Bpz * (r * cz(A_)));
+        const double la = lam_next[A_ * p.plane + o], lb = lam_next[B_ * p.plane + o];
+        lam_out[pull_index<A_>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, la, p.omega * (ev + od));
+        lam_out[pull_index<B_>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, lb, p.omega * (ev - od));
+    });
 }
 
 // lam_N(l,x,z) = dL[z] / Lx * (|xi_l - u|^2 - D T)/(D rho) at the stored state f.
