@@ -108,25 +108,39 @@ __device__ __forceinline__ bool ens_wait(const unsigned int* ctr, unsigned int n
 
 // extra_wait > 0 raises every barrier target so that it can never be met (a test of the
 // bounded wait: the launch must end with the error word set, not hang).
+// Per CTA, thread 0 fetches the next work item while the current tile computes, and keeps
+// the last completion count it saw for each lattice (up to ENS_CACHE lattices) so that the
+// many tiles of one (lattice, step) need a single acquire load of the global counter.
+constexpr int ENS_CACHE = 64;
+
 template <class P, int TZ>
 __global__ void __launch_bounds__(TZ, ens_min_blocks<TZ>())
 k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_tiles,
                  EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
     __shared__ int sbase[Q];
-    __shared__ unsigned int s_item;
+    __shared__ unsigned int s_item, s_next;
     __shared__ int s_ok;
+    __shared__ unsigned int s_seen[ENS_CACHE];
     const unsigned int total = (unsigned int)nsteps * (unsigned int)total_tiles;
+    for (int i = threadIdx.x; i < ENS_CACHE; i += blockDim.x) s_seen[i] = 0u;
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctl->queue, 1u);
+    __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned int it = atomicAdd(&ctl->queue, 1u);
+            const unsigned int it = s_next;
             int ok = 1;
             if (it < total) {
+                s_next = atomicAdd(&ctl->queue, 1u);        // next item, fetched ahead
                 const int s = (int)(it / (unsigned int)total_tiles);
                 const int b = (int)(it % (unsigned int)total_tiles);
                 const int i = ens_find(lats, n, b);
-                if (s > 0 || extra_wait)
-                    ok = ens_wait(&done[i], (unsigned int)s * (unsigned int)lats[i].ntiles + extra_wait,
-                                  &ctl->err, spin_limit);
+                if (s > 0 || extra_wait) {
+                    const unsigned int need = (unsigned int)s * (unsigned int)lats[i].ntiles + extra_wait;
+                    if (i >= ENS_CACHE || s_seen[i] < need) {
+                        ok = ens_wait(&done[i], need, &ctl->err, spin_limit);
+                        if (ok && i < ENS_CACHE) s_seen[i] = need;
+                    }
+                }
             }
             s_item = it;
             s_ok = ok;
