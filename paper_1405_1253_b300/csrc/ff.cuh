@@ -77,6 +77,46 @@ __device__ __forceinline__ ff ff_mul_f_u(ff a, float b) {
 
 __device__ __forceinline__ ff ff_renorm(ff a) { return fast_two_sum(a.hi, a.lo); }
 
+// a + 4 b when |a| >= |4 b| is known, not renormalised (4 b is exact, so the fast two-sum
+// error 4 b.hi - (s - a.hi) comes out of one FMA).
+__device__ __forceinline__ ff ff_add_big_u_x4(ff a, ff b) {
+    const float s = fmaf(4.0f, b.hi, a.hi);
+    const float e = fmaf(4.0f, b.hi, -(s - a.hi));
+    return ff{s, e + fmaf(4.0f, b.lo, a.lo)};
+}
+
+// A constant held as three FP32 terms (|hi + lo + lo2 - c| below 2^-70 |c|): products with
+// it carry no systematic error from the constant's representation.
+struct ff3 {
+    float hi, lo, lo2;
+};
+__device__ __forceinline__ ff3 ff3_of(const float (&t)[3]) { return ff3{t[0], t[1], t[2]}; }
+
+// a * c, renormalised (the a.lo * c.lo term, ~2^-48 relative, is dropped as in ff_mul).
+__device__ __forceinline__ ff ff_mul_c3(ff a, const ff3& c) {
+    const float p = a.hi * c.hi;
+    float e = fmaf(a.hi, c.hi, -p);
+    e = fmaf(a.hi, c.lo2, e);
+    e = fmaf(a.hi, c.lo, e);
+    e = fmaf(a.lo, c.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// Product with a power of two (exact).
+__device__ __forceinline__ ff ff_mul_pow2(ff a, float p2) { return ff{a.hi * p2, a.lo * p2}; }
+
+// 1 / a for a normalised a (|a.hi| a normal FP32 number, 1/a.hi too): the FP32 reciprocal y
+// refined by one Newton step that keeps the second-order term, 1/a = y (1 + e + e^2 + ...)
+// with e = 1 - a y (two FMAs; |e| ~ 2^-23 so e carries ~2^-47 absolute error), then
+// renormalised.  Relative error about 2^-47.
+__device__ __forceinline__ ff ff_rcp(ff a) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.hi));
+    float e = fmaf(-a.hi, y, 1.0f);
+    e = fmaf(-a.lo, y, e);
+    return fast_two_sum(y, y * fmaf(e, e, e));
+}
+
 // ---------------------------------------------------------------------------------
 // binary64 bit pattern (H = high word, L = low word) -> float-float.
 // hi = x rounded to 24 significant bits (half-up on the magnitude, by adding half of the
@@ -99,44 +139,43 @@ __device__ __forceinline__ ff bits_to_ff(uint32_t H, uint32_t L) {
 }
 
 // binary64 bit pattern -> signed 64-bit fixed point with unit 2^-60 (exact for
-// 2^-8 <= |x| < 4, truncated below 2^-60 for smaller |x|; |x| >= 4 is not representable).
+// 2^-8 <= |x| < 4 and x >= 0; bits below 2^-60 are dropped for smaller |x|).  A negative x
+// comes out in one's complement, i.e. one unit (2^-60) below its value, which keeps the
+// sign handling to two XORs; |x| >= 4 is not representable.
 __device__ __forceinline__ int64_t bits_to_fix60(uint32_t H, uint32_t L) {
-    const uint32_t Ha = H & 0x7FFFFFFFu;
-    const uint32_t n = 1025u - (Ha >> 20);                          // right shift of mant << 10
+    const uint32_t n = 1025u - ((H << 1) >> 21);                    // right shift of mant << 10
     // significand << 10 as two words: top 21 bits + the low word's top 22 bits, low word << 10
-    const uint32_t mh = __funnelshift_l(L, (Ha & 0x000FFFFFu) | 0x00100000u, 10);
+    const uint32_t mh = __funnelshift_l(L, (H & 0x000FFFFFu) | 0x00100000u, 10);
     const uint32_t ml = L << 10;
-    uint32_t vh, vl;
-    if (n < 32u) {                                                  // |x| >= 2^-22 (the usual case)
-        vl = __funnelshift_r(ml, mh, n);
-        vh = mh >> n;
-    } else {                                                        // tiny (or |x| >= 8: n wraps)
-        vl = n < 64u ? (mh >> (n - 32u)) : 0u;
-        vh = 0u;
-    }
-    const int64_t v = (int64_t)(((uint64_t)vh << 32) | vl);
-    return (H & 0x80000000u) ? -v : v;
+    // (mh:ml) >> n in two clamped funnel shifts: the first moves min(n, 32) bits, the
+    // second the rest (n >= 64 leaves nothing)
+    const int32_t n2 = max((int32_t)n - 32, 0);
+    const uint32_t vl0 = __funnelshift_rc(ml, mh, n);
+    const uint32_t vl = __funnelshift_rc(vl0, 0u, (uint32_t)n2);
+    const uint32_t vh = __funnelshift_rc(mh, 0u, n);
+    const uint32_t s = (uint32_t)((int32_t)H >> 31);
+    return (int64_t)((((uint64_t)(vh ^ s)) << 32) | (vl ^ s));
 }
 
 
-// Normalised float-float (|lo| <= ulp(hi)/2, hi a normal FP32 number) -> binary64,
-// rounded to nearest.
-// The pattern of (double)hi is built from the FP32 fields; lo is added as an integer
-// count of binary64 ulps of hi's binade (halved ulps when the sum drops below a power of two).
+// Normalised float-float (|lo| <= ulp(hi)/2, hi a normal FP32 number >= 2^-75 in
+// magnitude) -> binary64, rounded to nearest.
+// The pattern of (double)hi is built from the FP32 fields; lo is added as an integer count
+// of binary64 ulps of hi's binade.  When lo points towards zero the count is taken in the
+// ulps of the binade of hi's predecessor, which differs from hi's only when hi is a power
+// of two, exactly the case where the sum falls into the binade below.
 __device__ __forceinline__ double ff_to_double_bits(ff a) {
     const uint32_t hb = __float_as_uint(a.hi);
     const uint32_t ha = hb & 0x7FFFFFFFu;
     const uint32_t sgn = hb & 0x80000000u;
-    const uint32_t PH = (ha >> 3) + (896u << 20);
+    const uint32_t PH = (ha >> 3) + (896u << 20) + sgn;
     const uint32_t PL = ha << 29;
-    // scale 2^(52 - e_hi) carrying hi's sign: FP32 bits (306 - E8) << 23, E8 = hi's biased exponent
-    uint32_t sbits = (0x99000000u - (ha & 0x7F800000u)) | sgn;
-    // the sum drops into the binade below when hi is a power of two and lo points towards zero
-    if ((ha & 0x007FFFFFu) == 0u && ((__float_as_uint(a.lo) ^ hb) & 0x80000000u) && a.lo != 0.f)
-        sbits += (1u << 23);
+    const uint32_t m = (uint32_t)((int32_t)(__float_as_uint(a.lo) ^ hb) >> 31);   // 0 or ~0u
+    // scale 2^(52 - e) carrying hi's sign: FP32 bits (306 - E8) << 23 (+ sign)
+    const uint32_t sbits = 0x99000000u - ((hb + m) & 0x7F800000u) + sgn;
     const int32_t k = __float2int_rn(a.lo * __uint_as_float(sbits));
     const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (uint64_t)(int64_t)k;
-    return __hiloint2double((int)((uint32_t)(P >> 32) | sgn), (int)(uint32_t)P);
+    return __longlong_as_double((long long)P);
 }
 
 }  // namespace lbm

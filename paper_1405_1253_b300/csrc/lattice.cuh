@@ -66,9 +66,12 @@ static_assert(pair_first(NPAIR - 1) > 0 && pair_first(NPAIR) == -1, "18 opposite
 struct DevLattice {
     double w[NSHELL];      // shell weights
     double r, r2;          // lattice constant and its square
-    float wf_hi[NSHELL], wf_lo[NSHELL];  // float-float split of the weights
+    double r2_half;        // r^2 / 2
     float r_hi, r_lo, r2_hi, r2_lo;
     float wf[NSHELL];      // FP32 weights
+    // constants of the float-float collide as three FP32 terms each (no representation
+    // error that would bias every step): r, and 6 r^2, 12 r^2, 3 r^4 of the coefficients of 24 P(s)
+    float r3[3], r2x6[3], r2x12[3], r4x3[3];
 };
 
 // ----------------------------------------------------------------------------------

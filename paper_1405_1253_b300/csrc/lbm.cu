@@ -71,6 +71,10 @@ static bool g_quad_done = false;
 static Quadrature g_quad;
 static bool g_dev_uploaded[128];
 
+// Shell weights for kernel parameters; valid once a context exists (the quadrature is
+// solved before the first context is created and never changes afterwards).
+static const double* quad_w_shell() { return g_quad.w_shell; }
+
 static int host_quadrature(Quadrature* out) {
     std::lock_guard<std::mutex> lk(g_lat_mutex);
     if (!g_quad_done) {
@@ -87,6 +91,12 @@ static void split_ff(double v, float& hi, float& lo) {
     lo = (float)(v - (double)hi);
 }
 
+static void split3(long double v, float (&t)[3]) {
+    t[0] = (float)v;
+    t[1] = (float)(v - (long double)t[0]);
+    t[2] = (float)(v - (long double)t[0] - (long double)t[1]);
+}
+
 static int upload_lattice(int dev) {
     Quadrature q;
     int rc = host_quadrature(&q);
@@ -97,13 +107,18 @@ static int upload_lattice(int dev) {
     DevLattice h{};
     for (int s = 0; s < NSHELL; s++) {
         h.w[s] = q.w_shell[s];
-        split_ff(q.w_shell[s], h.wf_hi[s], h.wf_lo[s]);
         h.wf[s] = (float)q.w_shell[s];
     }
     h.r = q.r;
     h.r2 = q.r * q.r;
+    h.r2_half = 0.5 * h.r2;
     split_ff(h.r, h.r_hi, h.r_lo);
     split_ff(h.r2, h.r2_hi, h.r2_lo);
+    const long double rl = q.r, r2l = rl * rl;
+    split3(rl, h.r3);
+    split3(6.0L * r2l, h.r2x6);
+    split3(12.0L * r2l, h.r2x12);
+    split3(3.0L * r2l * r2l, h.r4x3);
     CU(cudaMemcpyToSymbol(d_lat, &h, sizeof h));
     PairInfo pairs[NPAIR];
     for (int k = 0; k < NPAIR; k++) {
@@ -364,7 +379,7 @@ int lbm_step(lbm_ctx* c, int nsteps) {
                 launch_step_f64((const double*)fin, (double*)fout, p, c->stream);
                 break;
             case LBM_F64_FF:
-                launch_step_ff((const double*)fin, (double*)fout, p, c->stream);
+                launch_step_ff((const double*)fin, (double*)fout, p, quad_w_shell(), c->stream);
                 break;
             default:
                 launch_step_f32((const float*)fin, (float*)fout, p, c->stream);
@@ -679,7 +694,7 @@ static int ens_launch(lbm_ensemble* e, int nsteps) {
     lbm_ctx* c0 = e->ctx[0];
     const StepParams p = step_params(c0);
     if (e->prec == LBM_F64_FF) {
-        const StepParamsFF q = ff_params(p);
+        const StepParamsFF q = ff_params(p, quad_w_shell());
         switch (e->tz) {
             case 64: return ens_launch_tz<StepParamsFF, 64>(e, q, nsteps);
             case 128: return ens_launch_tz<StepParamsFF, 128>(e, q, nsteps);

@@ -1,16 +1,19 @@
 // step_ff.cuh -- fused propagate + bc + collide with IEEE binary64 storage and an
-// FP64-accurate collide that stays off B300's slow FP64 pipe for all per-population work.
+// FP64-accurate collide that keeps B300's slow FP64 pipe for one FMA per population.
 //
 // B300 issues FP64 at about 1/64 of the FP32 rate (and every FP64 conversion at the same
 // rate), far below what 37 populations per site need at HBM speed.  Per site:
-//   1. the 37 pulled binary64 values are taken apart with integer instructions into
-//      a 64-bit fixed-point copy (unit 2^-60) and a float-float copy (ff.cuh);
-//   2. rho, J = sum c f and E = sum |c|^2 f are summed EXACTLY in 64-bit integers;
-//   3. the few per-site scalars (1/rho, u, T, the force shift) are formed in native FP64
-//      (about 30 FP64 instructions per site) and split into float-float;
-//   4. w f^eq_l = w w_l rho P(s), P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh),
-//      is evaluated in float-float, opposite velocities sharing the even part, and
-//      assembled into a binary64 pattern with integer instructions;
+//   1. the 37 pulled binary64 values are taken apart with integer instructions into a
+//      64-bit fixed-point copy (unit 2^-60, ff.cuh);
+//   2. rho, J = sum c f and E = sum |c|^2 f are summed in 64-bit integers;
+//   3. the per-site scalars (1/rho, u, T, the force shift) are formed in float-float from
+//      the four sums (four FP64 conversions and one FP64 FMA for T - 1, everything else on
+//      the FP32 pipes);
+//   4. 24 P(s), P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh), is evaluated in
+//      float-float with the factor 24 folded into the coefficients (so the s^3 and s^4 terms
+//      need no constant), opposite velocities sharing the even part; w f^eq_l = (w w_l / 24)
+//      rho * 24 P(s), the constant held in three FP32 terms so that no representation error
+//      of it biases every step, is assembled into a binary64 pattern with integer instructions;
 //   5. a second read of the populations (served by L1/L2, so DRAM sees each byte once)
 //      gives f' = (1 - w) g + w f^eq with one FP64 FMA per population.
 #pragma once
@@ -21,15 +24,18 @@ namespace lbm {
 
 struct StepParamsFF {
     int Lx, Lz, plane;
-    double omega, us_z, T_shift;   // FP64 per-site stage
-    double one_m_omega_d;          // the final f' = (1 - w) g + w f^eq is one FP64 FMA
-    ff c24, c6;                    // 1/24 and 1/6
+    double one_m_omega_d;   // the final f' = (1 - w) g + w f^eq is one FP64 FMA
+    ff3 wsh[NSHELL];        // w w_shell / 24 * 2^-60 (rho arrives in units of 2^-60)
+    ff us_z;                // tau (-g): velocity shift of the equilibrium
+    ff T_shift;             // tau (1 - tau) g^2 / D
 };
 
 // Split a double into float-float with integer instructions.
 __device__ __forceinline__ ff dsplit(double x) {
     return bits_to_ff((uint32_t)__double2hiint(x), (uint32_t)__double2loint(x));
 }
+// 64-bit integer -> float-float (one FP64 conversion, then the integer split).
+__device__ __forceinline__ ff i64_to_ff(int64_t v) { return dsplit(__ll2double_rn(v)); }
 
 template <bool WALL>
 __device__ __forceinline__ int pull_src(const SiteAddr& ad, const int* sbase, int l, int lop, int vx, int vz) {
@@ -40,7 +46,7 @@ __device__ __forceinline__ int pull_src(const SiteAddr& ad, const int* sbase, in
 template <bool WALL, class LD>
 __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* __restrict__ fout,
                                        const SiteAddr& ad, const int* sbase, const StepParamsFF& p) {
-    // -- pass 1: exact moments in 64-bit fixed point (all 37 loads in flight) -----------
+    // -- pass 1: moments in 64-bit fixed point (all 37 loads in flight) -------------------
     auto src1 = [&](auto tag) -> int {
         constexpr int L = decltype(tag)::value;
         if constexpr (WALL) return ad.template src<L, true>();
@@ -76,42 +82,47 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     });
     Jx = GX[1] + 2 * GX[2] + 3 * GX[3];
     Jz = GZ[1] + 2 * GZ[2] + 3 * GZ[3];
-    // -- per-site scalars in FP64 (the 2^60 scale cancels in the ratios) -----------------
-    const double r = d_lat.r;
-    const double rho_i = (double)R;
-    const double inv = 1.0 / rho_i;
-    const double ux = r * ((double)Jx * inv);
-    const double uz = r * ((double)Jz * inv);
-    const double T = 0.5 * (d_lat.r2 * ((double)E * inv) - (ux * ux + uz * uz));
-    const double usz = uz + p.us_z;
-    const double thd = (T - 1.0) + p.T_shift;
-    const double u2d = fma(ux, ux, usz * usz);
-    const double orhod = p.omega * (rho_i * 0x1p-60);
-    const ff a = dsplit(r * ux), b = dsplit(r * usz);
-    const ff th = dsplit(thd), u2 = dsplit(u2d), orho = dsplit(orhod);
-    // -- polynomial coefficients in float-float ---------------------------------------
-    const ff r2 = ff_make(d_lat.r2_hi, d_lat.r2_lo);
-    const ff thu2 = ff_mul(th, u2), th2 = ff_mul(th, th), u4 = ff_mul(u2, u2);
-    // k00 = 1 - u2/2 - th + u4/8 + th u2 + th^2; the |c|^2 coefficients carry r^2
-    ff k00 = ff_add(ff_make(1.0f, 0.0f), ff_mul_f_u(u2, -0.5f));
-    k00 = ff_add(k00, ff_add(ff_neg(th), ff_add(ff_mul_f_u(u4, 0.125f), ff_add(thu2, th2))));
-    const ff k01 = ff_mul(r2, ff_add(ff_mul_f_u(th, 0.5f), ff_neg(ff_add(ff_mul_f_u(thu2, 0.25f), th2))));
-    const ff k02 = ff_mul(ff_mul(r2, r2), ff_mul_f_u(th2, 0.125f));
-    const ff k10 = ff_add(ff_add(ff_make(1.0f, 0.0f), ff_mul_f_u(u2, -0.5f)), ff_mul_f_u(th, -2.0f));
-    const ff k11 = ff_mul(r2, ff_mul_f_u(th, 0.5f));
-    const ff k20 = ff_add(ff_add(ff_make(0.5f, 0.0f), ff_mul_f_u(u2, -0.25f)), ff_mul_f_u(th, -1.5f));
-    const ff k21 = ff_mul(r2, ff_mul_f_u(th, 0.25f));
+    // -- per-site scalars in float-float (the 2^60 scale cancels in the ratios) -----------
+    const double Rd = __ll2double_rn(R);
+    const ff rho = dsplit(Rd), jx = i64_to_ff(Jx), jz = i64_to_ff(Jz);
+    // T - 1 = (r^2 E / 2 - rho) / rho - |u|^2 / 2 (unshifted u).  The difference of the two
+    // O(1) terms is one FP64 FMA on the integer sums, so T - 1 keeps its relative accuracy
+    // (the K coefficients multiply it by up to ~|xi|^2 / 2).
+    const ff dT = dsplit(fma(d_lat.r2_half, __ll2double_rn(E), -Rd));
+    const ff inv = ff_rcp(rho);
+    const ff3 r = ff3_of(d_lat.r3);
+    const ff rinv = ff_mul_c3(inv, r);
+    const ff ux = ff_mul(jx, rinv), uz = ff_mul(jz, rinv);
+    const ff usz = ff_add(uz, p.us_z);                       // u_s = u + tau g
+    const ff ux2 = ff_mul_u(ux, ux);
+    const ff u2 = ff_add(ux2, ff_mul_u(usz, usz));
+    // th = T_s - 1 = T - 1 + T_shift
+    const ff th = ff_add(ff_sub(ff_mul_u(dT, inv), ff_mul_pow2(ff_add_u(ux2, ff_mul_u(uz, uz)), 0.5f)), p.T_shift);
+    const ff a = ff_mul_c3(ux, r), b = ff_mul_c3(usz, r);   // s_l = c_x a + c_z b
+    // -- coefficients of 24 K0, 24 K1, 24 K2 as polynomials in |c|^2 ------------------------
+    const ff th2 = ff_mul(th, th), thu2 = ff_mul(th, u2), u4 = ff_mul_u(u2, u2);
+    // 24 k00 = 24 - 12 u2 + 3 u4 + 24 (th u2 + th^2 - th)
+    const ff k00 = ff_add(ff_add(ff_make(24.0f, 0.0f), ff_mul_f_u(u2, -12.0f)),
+                          ff_add(ff_mul_f_u(u4, 3.0f), ff_mul_f_u(ff_add(thu2, ff_sub(th2, th)), 24.0f)));
+    // 24 k01 = 6 r^2 (2 th - th u2 - 4 th^2),  24 k02 = 3 r^4 th^2
+    const ff k01 = ff_mul_c3(ff_sub(ff_mul_pow2(th, 2.0f), ff_add(thu2, ff_mul_pow2(th2, 4.0f))), ff3_of(d_lat.r2x6));
+    const ff k02 = ff_mul_c3(th2, ff3_of(d_lat.r4x3));
+    // 24 k10 = 24 - 12 u2 - 48 th,  24 k11 = 12 r^2 th
+    const ff k10 = ff_add(ff_make(24.0f, 0.0f), ff_add(ff_mul_f_u(u2, -12.0f), ff_mul_f_u(th, -48.0f)));
+    const ff k11 = ff_mul_c3(th, ff3_of(d_lat.r2x12));
+    // 24 k20 = 12 - 6 u2 - 36 th,  24 k21 = 6 r^2 th
+    const ff k20 = ff_add(ff_make(12.0f, 0.0f), ff_add(ff_mul_f_u(u2, -6.0f), ff_mul_f_u(th, -36.0f)));
+    const ff k21 = ff_mul_c3(th, ff3_of(d_lat.r2x6));
     const int o = ad.dst();
     // -- pass 2: relaxation; rolled loops over shells and their pairs keep the code in
     //    the instruction cache, the shell coefficients are formed once per shell -------
     {
         const double v0 = LD::ld_again(fin + src1(Tag<0>{}));
-        const ff W0 = ff_mul(orho, ff_make(d_lat.wf_hi[0], d_lat.wf_lo[0]));
+        const ff W0 = ff_mul_c3(rho, p.wsh[0]);
         fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
     }
     // Loop over the shells; each shell (2 or 4 pairs) is processed two pairs at a time, so
-    // two independent dependency chains are in flight per thread.  The shell coefficients
-    // are formed once per shell; loops stay rolled to keep the code in the I-cache.
+    // two independent dependency chains are in flight per thread.
     auto pair_out = [&](const PairInfo& pi, const ff& K0, const ff& K1, const ff& K2, const ff& W,
                         double va, double vb) {
         // s = xi_A . u_s = c_x a + c_z b (left unnormalised)
@@ -119,9 +130,10 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const ff st = two_sum(sx.hi, sz.hi);
         const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
         const ff q = ff_mul_u(s, s);
-        // |K0| ~ 1 > |q K2|, |K2| ~ 1/2 > q/24, |K1| ~ 1 > q/6 and |Ev| > |Od| for |u| < 0.3
-        const ff Ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, ff_mul_u(q, p.c24))));
-        const ff Od = ff_mul_u(s, ff_add_big_u(K1, ff_mul_u(q, p.c6)));
+        // 24 P = [24 K0 + q (24 K2 + q)] + s [24 K1 + 4 q]; |24 K0| ~ 24 > q |24 K2 + q|,
+        // |24 K2| ~ 12 > q, |24 K1| ~ 24 > 4 q and the even part exceeds the odd one for |u| < 0.3
+        const ff Ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, q)));
+        const ff Od = ff_mul_u(s, ff_add_big_u_x4(K1, q));
         const ff Pa = ff_mul_u(W, Ev), Pb = ff_mul_u(W, Od);
         // w f^eq of the pair in binary64, then f' = (1 - w) g + w f^eq by one FP64 FMA each
         const double Xp = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, Pb)));
@@ -136,7 +148,7 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
         const ff K0 = ff_add_u(k00, ff_mul_f_u(ff_add_u(k01, ff_mul_f_u(k02, C2)), C2));
         const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
         const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
-        const ff W = ff_mul(orho, ff_make(d_lat.wf_hi[sh], d_lat.wf_lo[sh]));
+        const ff W = ff_mul_c3(rho, p.wsh[sh]);
 #pragma unroll 1
         for (int k = k0; k < k1; k += 2) {            // every shell has an even number of pairs
             const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
@@ -181,20 +193,28 @@ inline ff ff_host(double v) {
     return r;
 }
 
-inline StepParamsFF ff_params(const StepParams& p) {
+inline ff3 ff3_host(long double v) {
+    ff3 r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (long double)r.hi);
+    r.lo2 = (float)(v - (long double)r.hi - (long double)r.lo);
+    return r;
+}
+
+// w_shell: the shell weights (binary64).
+inline StepParamsFF ff_params(const StepParams& p, const double* w_shell) {
     StepParamsFF q;
     q.Lx = p.Lx; q.Lz = p.Lz; q.plane = p.plane;
-    q.omega = p.omega;
-    q.us_z = p.us_z;
-    q.T_shift = p.T_shift;
     q.one_m_omega_d = p.one_m_omega;
-    q.c24 = ff_host(1.0 / 24.0);
-    q.c6 = ff_host(1.0 / 6.0);
+    for (int sh = 0; sh < NSHELL; sh++) q.wsh[sh] = ff3_host((long double)p.omega * w_shell[sh] / 24.0L * 0x1p-60L);
+    q.us_z = ff_host(p.us_z);
+    q.T_shift = ff_host(p.T_shift);
     return q;
 }
 
-inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, cudaStream_t st) {
-    const StepParamsFF q = ff_params(p);
+inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, const double* w_shell,
+                           cudaStream_t st) {
+    const StepParamsFF q = ff_params(p, w_shell);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     k_step_ff<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
