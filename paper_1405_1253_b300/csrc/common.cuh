@@ -36,9 +36,11 @@ struct StepParams {
     double grav;             // g >= 0
 };
 
-// x index wrapped into [0, Lx) for |k| <= 3 (any Lx >= 1).
+// x index v = x + k (0 <= x < Lx, |k| <= 3) wrapped into [0, Lx) (any Lx >= 1; one
+// compare-and-add for Lx >= 3, a remainder only for the narrower lattices).
 __device__ __forceinline__ int wrap_x(int v, int Lx) {
-    int t = v % Lx;
+    if (Lx >= 3) return v < 0 ? v + Lx : (v >= Lx ? v - Lx : v);
+    const int t = v % Lx;
     return t < 0 ? t + Lx : t;
 }
 
@@ -151,10 +153,11 @@ struct LoadCG {
 };
 
 // Interior tiles: sbase[l] = l * plane + wrap(x - c_lx) * Lz - c_lz, so that the pull
-// source of population l at row z is sbase[l] + z.  Filled by the first Q threads.
+// source of population l at row z is sbase[l] + z.  Filled by the block's threads in
+// turn (every entry is written for any block size).
 __device__ __forceinline__ void fill_pull_bases(int* sbase, int x, int Lx, int Lz, int plane) {
-    const int l = threadIdx.x;
-    if (l < Q) sbase[l] = l * plane + wrap_x(x - d_vel[l][0], Lx) * Lz - d_vel[l][1];
+    for (int l = threadIdx.x; l < Q; l += blockDim.x)
+        sbase[l] = l * plane + wrap_x(x - d_vel[l][0], Lx) * Lz - d_vel[l][1];
 }
 
 // Compile-time loop: calls f(Tag<L>{}) for L = 0..N-1.
