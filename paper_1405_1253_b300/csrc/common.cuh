@@ -13,7 +13,7 @@ __constant__ DevLattice d_lat;
 // (filled from the compile-time tables of lattice.cuh at upload).
 struct PairInfo {
     int A, B, cx, cz, c2, shell;
-    float fcx, fcz, fc2, pad;   // the same integers as FP32 (no conversion in the loop)
+    float fcx, fcz, fc2;        // the same integers as FP32 (no conversion in the loop)
 };
 __constant__ PairInfo d_pairs[18];
 // Pairs are grouped by shell in canonical order: shell s owns pairs

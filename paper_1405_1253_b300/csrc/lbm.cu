@@ -123,7 +123,7 @@ static int upload_lattice(int dev) {
     PairInfo pairs[NPAIR];
     for (int k = 0; k < NPAIR; k++) {
         const int A = pair_first(k);
-        pairs[k] = PairInfo{A, opp(A), cx(A), cz(A), c2(A), shell_of(A), (float)cx(A), (float)cz(A), (float)c2(A), 0.f};
+        pairs[k] = PairInfo{A, opp(A), cx(A), cz(A), c2(A), shell_of(A), (float)cx(A), (float)cz(A), (float)c2(A)};
     }
     CU(cudaMemcpyToSymbol(d_pairs, pairs, sizeof pairs));
     int sfirst[NSHELL] = {0}, snp[NSHELL] = {0}, vel[Q][2];

@@ -37,33 +37,50 @@ __device__ __forceinline__ ff dsplit(double x) {
 // 64-bit integer -> float-float (one FP64 conversion, then the integer split).
 __device__ __forceinline__ ff i64_to_ff(int64_t v) { return dsplit(__ll2double_rn(v)); }
 
-template <bool WALL>
-__device__ __forceinline__ int pull_src(const SiteAddr& ad, const int* sbase, int l, int lop, int vx, int vz) {
-    if constexpr (WALL) return ad.template src_rt<true>(l, lop, vx, vz);
-    else return sbase[l] + ad.z;
-}
-
+// Pull sources of one site, read from global memory (interior sites through the pull bases
+// of the tile, wall sites through the bounce-back rule).
 template <bool WALL, class LD>
-__device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* __restrict__ fout,
-                                       const SiteAddr& ad, const int* sbase, const StepParamsFF& p) {
-    // -- pass 1: moments in 64-bit fixed point (all 37 loads in flight) -------------------
-    auto src1 = [&](auto tag) -> int {
-        constexpr int L = decltype(tag)::value;
+struct SrcGlobal {
+    const double* __restrict__ fin;
+    const SiteAddr& ad;
+    const int* sbase;     // interior pull bases (fill_pull_bases)
+    template <int L>
+    __device__ __forceinline__ int idx() const {
         if constexpr (WALL) return ad.template src<L, true>();
         else return sbase[L] + ad.z;
-    };
+    }
+    template <int L>
+    __device__ __forceinline__ double first() const { return LD::ld(fin + idx<L>()); }
+    template <int L>
+    __device__ __forceinline__ double again() const { return LD::ld_again(fin + idx<L>()); }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
+        if constexpr (WALL) {
+            va = LD::ld_again(fin + ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz));
+            vb = LD::ld_again(fin + ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz));
+        } else {
+            va = LD::ld_again(fin + sbase[pi.A] + ad.z);
+            vb = LD::ld_again(fin + sbase[pi.B] + ad.z);
+        }
+    }
+};
+
+// The collide of one site: src gives the 37 pulled populations, the results go to
+// fout[l * plane + o].
+template <class SRC>
+__device__ __forceinline__ void site_ff(const SRC& src, double* __restrict__ fout, int o, const StepParamsFF& p) {
+    // -- pass 1: moments in 64-bit fixed point ---------------------------------------------
     // pair sums by shell, pair differences grouped by |c_x| and |c_z| (no multiplies)
     int64_t R, Jx, Jz, E = 0;
     int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t GX[4] = {0, 0, 0, 0}, GZ[4] = {0, 0, 0, 0};
     {
-        const double v0 = LD::ld(fin + src1(Tag<0>{}));
+        const double v0 = src.template first<0>();
         R = bits_to_fix60((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
     }
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        const double va = LD::ld(fin + src1(Tag<A>{}));
-        const double vb = LD::ld(fin + src1(Tag<B>{}));
+        const double va = src.template first<A>();
+        const double vb = src.template first<B>();
         const int64_t fa = bits_to_fix60((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
         const int64_t fb = bits_to_fix60((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
         S[shell_of(A)] += fa + fb;
@@ -113,11 +130,10 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
     // 24 k20 = 12 - 6 u2 - 36 th,  24 k21 = 6 r^2 th
     const ff k20 = ff_add(ff_make(12.0f, 0.0f), ff_add(ff_mul_f_u(u2, -6.0f), ff_mul_f_u(th, -36.0f)));
     const ff k21 = ff_mul_c3(th, ff3_of(d_lat.r2x6));
-    const int o = ad.dst();
     // -- pass 2: relaxation; rolled loops over shells and their pairs keep the code in
     //    the instruction cache, the shell coefficients are formed once per shell -------
     {
-        const double v0 = LD::ld_again(fin + src1(Tag<0>{}));
+        const double v0 = src.template again<0>();
         const ff W0 = ff_mul_c3(rho, p.wsh[0]);
         fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
     }
@@ -152,18 +168,17 @@ __device__ __forceinline__ void site_ff(const double* __restrict__ fin, double* 
 #pragma unroll 1
         for (int k = k0; k < k1; k += 2) {            // every shell has an even number of pairs
             const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
-            const double v0a = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p0.A, p0.B, p0.cx, p0.cz));
-            const double v0b = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p0.B, p0.A, -p0.cx, -p0.cz));
-            const double v1a = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p1.A, p1.B, p1.cx, p1.cz));
-            const double v1b = LD::ld_again(fin + pull_src<WALL>(ad, sbase, p1.B, p1.A, -p1.cx, -p1.cz));
+            double v0a, v0b, v1a, v1b;
+            src.pair(p0, v0a, v0b);
+            src.pair(p1, v1a, v1b);
             pair_out(p0, K0, K1, K2, W, v0a, v0b);
             pair_out(p1, K0, K1, K2, W, v1a, v1b);
         }
     }
 }
 
-// One tile b of the lattice tiling t; sbase: Q ints of shared memory.  All threads of the
-// block must call this (it synchronises once after filling sbase).
+// One tile b of the lattice tiling t, pulled from global memory; sbase: Q ints of shared
+// memory.  All threads of the block must call this (it synchronises once after filling sbase).
 template <class LD>
 __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
                                        const StepParamsFF& p, Tiling t, int b, int* sbase) {
@@ -175,8 +190,8 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
     SiteAddr ad;
     bool wall;
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    if (wall) site_ff<true, LD>(fin, fout, ad, sbase, p);
-    else site_ff<false, LD>(fin, fout, ad, sbase, p);
+    if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, fout, ad.dst(), p);
+    else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, fout, ad.dst(), p);
 }
 
 // 7 resident blocks per SM (72 registers, 28 warps): measured best; 8 spills
@@ -218,5 +233,6 @@ inline void launch_step_ff(const double* fin, double* fout, const StepParams& p,
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     k_step_ff<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
+
 
 }  // namespace lbm
