@@ -46,21 +46,28 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def csrc_hash() -> str:
+# The sources that define each step kernel (its counters stay valid while these are unchanged).
+KERNEL_SOURCES = {
+    "k_step_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh"),
+    "k_step_f64": ("lattice.cuh", "common.cuh", "step_f64.cuh"),
+    "k_step_f32": ("lattice.cuh", "common.cuh", "step_f32.cuh"),
+}
+
+
+def kernel_hash(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1405_1253_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, sites: int):
     """Per-launch DRAM bytes from profiles/, if taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    want = csrc_hash()
+    want = kernel_hash(kernel)
     for line in open(path):
         m = re.match(r"TRAFFIC kernel=(\S+) src=(\S+) bytes_per_site=([0-9.eE+-]+)", line.strip())
         if m and m.group(1) == kernel and m.group(2) == want:

@@ -55,11 +55,10 @@ enum {
  *   LBM_F64_FF  IEEE binary64 storage, collide in float-float arithmetic (pairs of
  *               FP32 carrying a ~48-bit significand) on the FP32 and integer pipes;
  *               same storage and bytes as LBM_F64, results equal to ~1e-14 per step.
- *   LBM_F32     FP32 storage, FP32 collide arithmetic.
- *   LBM_F32_DEV FP32 storage of the deviation f - f_ref(l, z) from a per-row FP64
- *               reference equilibrium (the unperturbed layers) fixed at
- *               lbm_init_layers; FP32 collide arithmetic.                            */
-typedef enum { LBM_F64 = 0, LBM_F64_FF = 1, LBM_F32 = 2, LBM_F32_DEV = 3 } lbm_prec;
+ *   LBM_F32     FP32 storage, FP32 collide arithmetic (compensated moment sums; the
+ *               collide update is repaired to conserve mass, momentum + rho g and
+ *               internal energy).                                                     */
+typedef enum { LBM_F64 = 0, LBM_F64_FF = 1, LBM_F32 = 2 } lbm_prec;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque */
 
@@ -83,11 +82,11 @@ typedef struct {
 
 /* Create a context for an Lx x Lz lattice with relaxation time tau > 0.5 and gravity
  * g >= 0 (Sec. III.A).  buf0 and buf1 are 16-byte aligned device buffers on one device
- * of at least 37*Lx*Lz*(8 for LBM_F64 / LBM_F64_FF, 4 for LBM_F32 / LBM_F32_DEV) bytes
+ * of at least 37*Lx*Lz*(8 for LBM_F64 / LBM_F64_FF, 4 for LBM_F32) bytes
  * each, `bytes` the size of each; they hold the two lattice copies (Sec. III.B: read
  * one, write the other, swap).  The state starts in buf0.  cuda_stream is a
  * cudaStream_t (NULL: the legacy default stream).  The context allocates only small
- * private scratch (reduction partials, per-row references, mode parameters).  On
+ * private scratch (reduction partials, mode parameters, an error word).  On
  * failure *out is NULL.                                                               */
 int lbm_create(lbm_ctx **out, int Lx, int Lz, int prec, double tau, double g,
                void *buf0, void *buf1, size_t bytes, void *cuda_stream);
@@ -111,8 +110,7 @@ void *lbm_current(lbm_ctx *c);
 
 /* Copy the current state out / in as canonical FP64 f[l][x][z] (37*Lx*Lz doubles).
  * on_device = 1: `f` is a device pointer (stream-ordered, asynchronous); 0: a host
- * pointer (the call synchronises).  FP32 storage is converted; for LBM_F32_DEV the
- * per-row reference is added back / subtracted.                                       */
+ * pointer (the call synchronises).  FP32 storage is converted.                        */
 int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
 int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
 

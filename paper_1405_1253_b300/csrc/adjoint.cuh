@@ -136,7 +136,7 @@ __global__ void k_loss_adjoint(const double* __restrict__ f, const double* __res
     const int x = blockIdx.y;
     if (z >= Lz) return;
     double R, ux, uz, T;
-    site_moments<StoreF64>(f, nullptr, x, z, Lz, Lx * Lz, R, ux, uz, T);
+    site_moments<StoreF64>(f, x, z, Lz, Lx * Lz, R, ux, uz, T);
     const double scale = dL[z] / (double)Lx / (DIM * R);
     const int o = x * Lz + z;
 #pragma unroll

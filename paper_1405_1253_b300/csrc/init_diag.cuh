@@ -7,27 +7,16 @@ namespace lbm {
 
 // ---------------------------------------------------------------------------------
 // Storage policies: how a stored population is read as FP64 / written from FP64.
-// F32_DEV stores f - ref(l, z) where ref ([Q][Lz], FP64) is a per-row reference.
 // ---------------------------------------------------------------------------------
 struct StoreF64 {
     using T = double;
-    __device__ static double get(const double* f, int idx, int, const double*) { return f[idx]; }
-    __device__ static void put(double* f, int idx, double v, int, const double*) { f[idx] = v; }
+    __device__ static double get(const double* f, int idx) { return f[idx]; }
+    __device__ static void put(double* f, int idx, double v) { f[idx] = v; }
 };
 struct StoreF32 {
     using T = float;
-    __device__ static double get(const float* f, int idx, int, const double*) { return (double)f[idx]; }
-    __device__ static void put(float* f, int idx, double v, int, const double*) { f[idx] = (float)v; }
-};
-struct StoreF32Dev {
-    using T = float;
-    // lz = l * Lz + z selects the row reference of the stored element
-    __device__ static double get(const float* f, int idx, int lz, const double* ref) {
-        return (double)f[idx] + ref[lz];
-    }
-    __device__ static void put(float* f, int idx, double v, int lz, const double* ref) {
-        f[idx] = (float)(v - ref[lz]);
-    }
+    __device__ static double get(const float* f, int idx) { return (double)f[idx]; }
+    __device__ static void put(float* f, int idx, double v) { f[idx] = (float)v; }
 };
 
 // ---------------------------------------------------------------------------------
@@ -90,23 +79,8 @@ __device__ __forceinline__ void layer_p_T(double z, double zl, double zh, const 
               + (ip.Td - ip.Tm) * 0.5 * (1.0 - tanh((z - zl) / ip.wt));
 }
 
-// Per-row reference equilibrium of the unperturbed layers (FP32 deviation storage).
-__global__ void k_rowref(double* __restrict__ ref, float* __restrict__ ref32, InitParams ip) {
-    const int z = blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= ip.Lz) return;
-    double p, T, f[Q];
-    layer_p_T(z + 0.5, ip.zlo0, ip.zhi0, ip, p, T);
-    feq_f64(p / T, 0.0, -0.5 * ip.grav, T, f);
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        ref[l * ip.Lz + z] = f[l];
-        ref32[l * ip.Lz + z] = (float)f[l];
-    }
-}
-
 template <class S>
-__global__ void k_init(typename S::T* __restrict__ f, const double* __restrict__ zc,
-                       const double* __restrict__ ref, InitParams ip) {
+__global__ void k_init(typename S::T* __restrict__ f, const double* __restrict__ zc, InitParams ip) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int x = blockIdx.y;
     if (z >= ip.Lz) return;
@@ -115,21 +89,21 @@ __global__ void k_init(typename S::T* __restrict__ f, const double* __restrict__
     feq_f64(p / T, 0.0, -0.5 * ip.grav, T, fe);
     const int o = x * ip.Lz + z;
 #pragma unroll
-    for (int l = 0; l < Q; l++) S::put(f, l * ip.plane + o, fe[l], l * ip.Lz + z, ref);
+    for (int l = 0; l < Q; l++) S::put(f, l * ip.plane + o, fe[l]);
 }
 
 // ---------------------------------------------------------------------------------
 // Moments of the stored populations (Sec. III.A).
 // ---------------------------------------------------------------------------------
 template <class S>
-__device__ __forceinline__ void site_moments(const typename S::T* f, const double* ref, int x, int z,
+__device__ __forceinline__ void site_moments(const typename S::T* f, int x, int z,
                                              int Lz, int plane, double& rho, double& ux, double& uz,
                                              double& T) {
     const int o = x * Lz + z;
     double R = 0.0, Jx = 0.0, Jz = 0.0, E = 0.0;
 #pragma unroll
     for (int l = 0; l < Q; l++) {
-        const double v = S::get(f, l * plane + o, l * Lz + z, ref);
+        const double v = S::get(f, l * plane + o);
         R += v;
         Jx += cx(l) * v;
         Jz += cz(l) * v;
@@ -142,14 +116,13 @@ __device__ __forceinline__ void site_moments(const typename S::T* f, const doubl
 }
 
 template <class S>
-__global__ void k_moments(const typename S::T* __restrict__ f, const double* __restrict__ ref, int Lx,
-                          int Lz, double grav, int renorm, double* rho, double* ux, double* uz,
+__global__ void k_moments(const typename S::T* __restrict__ f, int Lx, int Lz, double grav, int renorm, double* rho, double* ux, double* uz,
                           double* T) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int x = blockIdx.y;
     if (z >= Lz) return;
     double R, U, V, TT;
-    site_moments<S>(f, ref, x, z, Lz, Lx * Lz, R, U, V, TT);
+    site_moments<S>(f, x, z, Lz, Lx * Lz, R, U, V, TT);
     if (renorm) {              // u^H = u_stored - gvec/2, T^H = T + g^2/(4 D)
         V += 0.5 * grav;
         TT += grav * grav / (4.0 * DIM);
@@ -163,8 +136,8 @@ __global__ void k_moments(const typename S::T* __restrict__ f, const double* __r
 
 // Horizontal mean of T, stage 1: columns [c*nx_per, (c+1)*nx_per) summed into part[c][z].
 template <class S>
-__global__ void k_rowT_partial(const typename S::T* __restrict__ f, const double* __restrict__ ref, int Lx,
-                               int Lz, int nx_per, double* __restrict__ part) {
+__global__ void k_rowT_partial(const typename S::T* __restrict__ f, int Lx, int Lz, int nx_per,
+                               double* __restrict__ part) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (z >= Lz) return;
@@ -172,7 +145,7 @@ __global__ void k_rowT_partial(const typename S::T* __restrict__ f, const double
     double s = 0.0;
     for (int x = x0; x < x1; x++) {
         double R, U, V, TT;
-        site_moments<S>(f, ref, x, z, Lz, Lx * Lz, R, U, V, TT);
+        site_moments<S>(f, x, z, Lz, Lx * Lz, R, U, V, TT);
         s += TT;
     }
     part[c * Lz + z] = s;
@@ -193,16 +166,14 @@ constexpr int RED_THREADS = 256;
 
 template <class S>
 __global__ void __launch_bounds__(RED_THREADS)
-k_global_partial(const typename S::T* __restrict__ f, const double* __restrict__ ref, int Lx, int Lz,
-                 double* __restrict__ part) {
+k_global_partial(const typename S::T* __restrict__ f, int Lx, int Lz, double* __restrict__ part) {
     __shared__ double sm[2][RED_THREADS];
     const int nsite = Lx * Lz;
     double m = 0.0, e = 0.0;
     for (int s = blockIdx.x * RED_THREADS + threadIdx.x; s < nsite; s += gridDim.x * RED_THREADS) {
-        const int z = s % Lz;
 #pragma unroll
         for (int l = 0; l < Q; l++) {
-            const double v = S::get(f, l * nsite + s, l * Lz + z, ref);
+            const double v = S::get(f, l * nsite + s);
             m += v;
             e += c2(l) * v;
         }
@@ -310,25 +281,19 @@ __global__ void k_widths(const double* __restrict__ Tbar, int Lz, double Tu, dou
 // Storage <-> canonical FP64 conversion of n elements starting at element `first`.
 // ---------------------------------------------------------------------------------
 template <class S>
-__global__ void k_to_f64(const typename S::T* __restrict__ f, const double* __restrict__ ref, long long first,
-                         long long n, int Lx, int Lz, double* __restrict__ out) {
+__global__ void k_to_f64(const typename S::T* __restrict__ f, long long first, long long n,
+                         double* __restrict__ out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const long long e = first + i;
-    const int z = (int)(e % Lz);
-    const int l = (int)(e / ((long long)Lx * Lz));
-    out[i] = S::get(f, (int)e, l * Lz + z, ref);
+    out[i] = S::get(f, (int)(first + i));
 }
 
 template <class S>
-__global__ void k_from_f64(typename S::T* __restrict__ f, const double* __restrict__ ref, long long first,
-                           long long n, int Lx, int Lz, const double* __restrict__ in) {
+__global__ void k_from_f64(typename S::T* __restrict__ f, long long first, long long n,
+                           const double* __restrict__ in) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const long long e = first + i;
-    const int z = (int)(e % Lz);
-    const int l = (int)(e / ((long long)Lx * Lz));
-    S::put(f, (int)e, in[i], l * Lz + z, ref);
+    S::put(f, (int)(first + i), in[i]);
 }
 
 }  // namespace lbm

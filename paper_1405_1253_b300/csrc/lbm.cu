@@ -152,8 +152,6 @@ struct lbm_ctx {
     double* zcol = nullptr;     // 2 * Lx interface heights / per-column adjoint sums
     double* modes = nullptr;    // 4 * modes_cap mode parameters
     int modes_cap = 0;
-    double* rowref = nullptr;   // Q * Lz per-row reference (LBM_F32_DEV)
-    float* rowref32 = nullptr;  // same in FP32
     double* part = nullptr;     // reduction partials
     size_t part_cap = 0;        // in doubles
     double* small = nullptr;    // Lz + 8 doubles (Tbar, widths, sums)
@@ -193,7 +191,7 @@ static int ensure_part(lbm_ctx* c, size_t n) {
 
 static void free_ctx(lbm_ctx* c) {
     if (!c) return;
-    void* ps[] = {c->zcol, c->modes, c->rowref, c->rowref32, c->part, c->small, c->dLrow, c->colred, c->err};
+    void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete c;
@@ -202,8 +200,8 @@ static void free_ctx(lbm_ctx* c) {
 template <class S>
 static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renorm) {
     dim3 grid((c->Lz + 127) / 128, c->Lx);
-    k_moments<S><<<grid, 128, 0, c->stream>>>((const typename S::T*)c->buf[c->cur], c->rowref, c->Lx, c->Lz,
-                                              c->grav, renorm, rho, ux, uz, T);
+    k_moments<S><<<grid, 128, 0, c->stream>>>((const typename S::T*)c->buf[c->cur], c->Lx, c->Lz, c->grav, renorm,
+                                              rho, ux, uz, T);
 }
 
 extern "C" {
@@ -229,8 +227,7 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     if (Lx < 1 || Lz < 6) return fail(LBM_EINVAL, "lattice %d x %d: need Lx >= 1, Lz >= 6", Lx, Lz);
     if ((long long)Q * Lx * Lz >= (1LL << 31))
         return fail(LBM_EINVAL, "lattice %d x %d too large: 37*Lx*Lz must be < 2^31", Lx, Lz);
-    if (prec < LBM_F64 || prec > LBM_F32_DEV) return fail(LBM_EINVAL, "unknown precision %d", prec);
-    if (prec == LBM_F32_DEV) return fail(LBM_EINVAL, "LBM_F32_DEV is not available in this build");
+    if (prec < LBM_F64 || prec > LBM_F32) return fail(LBM_EINVAL, "unknown precision %d", prec);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_EINVAL, "tau = %g must be > 0.5", tau);
     if (!(g >= 0.0) || !std::isfinite(g)) return fail(LBM_EINVAL, "g = %g must be >= 0", g);
     if (!buf0 || !buf1 || buf0 == buf1) return fail(LBM_EINVAL, "need two distinct device buffers");
@@ -256,9 +253,6 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
               cudaMalloc(&c->dLrow, (size_t)Lz * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->colred, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->err, sizeof(unsigned int)) == cudaSuccess;
-    if (ok && prec == LBM_F32_DEV)
-        ok = cudaMalloc(&c->rowref, (size_t)Q * Lz * sizeof(double)) == cudaSuccess &&
-             cudaMalloc(&c->rowref32, (size_t)Q * Lz * sizeof(float)) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
         return fail(LBM_ENOMEM, "context scratch allocation failed");
@@ -348,15 +342,10 @@ int lbm_init_layers(lbm_ctx* c, const lbm_layers_desc* d) {
     switch (c->prec) {
         case LBM_F64:
         case LBM_F64_FF:
-            k_init<StoreF64><<<grid, 128, 0, c->stream>>>((double*)f, c->zcol, nullptr, ip);
-            break;
-        case LBM_F32:
-            k_init<StoreF32><<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, nullptr, ip);
+            k_init<StoreF64><<<grid, 128, 0, c->stream>>>((double*)f, c->zcol, ip);
             break;
         default:
-            k_rowref<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->rowref, c->rowref32, ip);
-            LAUNCH_CHECK();
-            k_init<StoreF32Dev><<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, c->rowref, ip);
+            k_init<StoreF32><<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, ip);
             break;
     }
     LAUNCH_CHECK();
@@ -410,20 +399,17 @@ static int convert_pops(lbm_ctx* c, double* buf, int on_device, bool to_f64) {
     double* tmp = nullptr;
     if (!on_device && cudaMallocAsync((void**)&tmp, chunk * sizeof(double), c->stream) != cudaSuccess)
         return fail(LBM_ENOMEM, "conversion buffer allocation failed");
-    const double* ref = c->rowref;
     for (long long first = 0; first < n; first += chunk) {
         const long long m = std::min(chunk, n - first);
         double* dev = on_device ? buf + first : tmp;
         const int blocks = (int)((m + 255) / 256);
         if (to_f64) {
-            if (c->prec == LBM_F32) k_to_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
-            else k_to_f64<StoreF32Dev><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            k_to_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
             LAUNCH_CHECK();
             if (!on_device) CU(cudaMemcpyAsync(buf + first, tmp, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         } else {
             if (!on_device) CU(cudaMemcpyAsync(tmp, buf + first, m * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-            if (c->prec == LBM_F32) k_from_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
-            else k_from_f64<StoreF32Dev><<<blocks, 256, 0, c->stream>>>((float*)f, ref, first, m, c->Lx, c->Lz, dev);
+            k_from_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
             LAUNCH_CHECK();
         }
         if (!on_device) CU(cudaStreamSynchronize(c->stream));
@@ -468,8 +454,7 @@ int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int 
     }
     switch (c->prec) {
         case LBM_F64: case LBM_F64_FF: launch_moments<StoreF64>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
-        case LBM_F32: launch_moments<StoreF32>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
-        default: launch_moments<StoreF32Dev>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+        default: launch_moments<StoreF32>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
     }
     LAUNCH_CHECK();
     if (!on_device) {
@@ -491,11 +476,9 @@ static int row_mean_device(lbm_ctx* c, double* Tbar_dev) {
     const void* f = c->buf[c->cur];
     switch (c->prec) {
         case LBM_F64: case LBM_F64_FF:
-            k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, nullptr, c->Lx, c->Lz, nx_per, c->part); break;
-        case LBM_F32:
-            k_rowT_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, nullptr, c->Lx, c->Lz, nx_per, c->part); break;
+            k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, nx_per, c->part); break;
         default:
-            k_rowT_partial<StoreF32Dev><<<grid, 128, 0, c->stream>>>((const float*)f, c->rowref, c->Lx, c->Lz, nx_per, c->part); break;
+            k_rowT_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, c->Lx, c->Lz, nx_per, c->part); break;
     }
     LAUNCH_CHECK();
     k_rowT_final<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->part, nch, c->Lx, c->Lz, Tbar_dev);
@@ -545,11 +528,9 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
     const void* f = c->buf[c->cur];
     switch (c->prec) {
         case LBM_F64: case LBM_F64_FF:
-            k_global_partial<StoreF64><<<nblk, RED_THREADS, 0, c->stream>>>((const double*)f, nullptr, c->Lx, c->Lz, c->part); break;
-        case LBM_F32:
-            k_global_partial<StoreF32><<<nblk, RED_THREADS, 0, c->stream>>>((const float*)f, nullptr, c->Lx, c->Lz, c->part); break;
+            k_global_partial<StoreF64><<<nblk, RED_THREADS, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, c->part); break;
         default:
-            k_global_partial<StoreF32Dev><<<nblk, RED_THREADS, 0, c->stream>>>((const float*)f, c->rowref, c->Lx, c->Lz, c->part); break;
+            k_global_partial<StoreF32><<<nblk, RED_THREADS, 0, c->stream>>>((const float*)f, c->Lx, c->Lz, c->part); break;
     }
     LAUNCH_CHECK();
     k_global_final<<<1, RED_THREADS, 0, c->stream>>>(c->part, nblk, c->small);
@@ -954,7 +935,7 @@ extern "C" int lbm_row_mean_T_noalloc(const double* f, int Lx, int Lz, double* T
     const int nch = (Lx + nx_per - 1) / nx_per;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     dim3 grid((Lz + 127) / 128, nch);
-    k_rowT_partial<StoreF64><<<grid, 128, 0, st>>>(f, nullptr, Lx, Lz, nx_per, scratch);
+    k_rowT_partial<StoreF64><<<grid, 128, 0, st>>>(f, Lx, Lz, nx_per, scratch);
     LAUNCH_CHECK();
     k_rowT_final<<<(Lz + 127) / 128, 128, 0, st>>>(scratch, nch, Lx, Lz, Tbar);
     LAUNCH_CHECK();

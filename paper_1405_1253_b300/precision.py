@@ -39,7 +39,7 @@ def main():
     ap.add_argument("--Lx", type=int, default=W.PRECISION_4096x8192.Lx)
     ap.add_argument("--Lz", type=int, default=W.PRECISION_4096x8192.Lz)
     ap.add_argument("--steps", type=int, default=W.PRECISION_STEPS)
-    ap.add_argument("--low", default="f32", choices=["f32", "f32_dev"])
+    ap.add_argument("--low", default="f32", choices=["f32"])
     args = ap.parse_args()
     import torch
     from . import lbm
