@@ -58,8 +58,8 @@ struct SrcGlobal {
             va = LD::ld_again(fin + ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz));
             vb = LD::ld_again(fin + ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz));
         } else {
-            va = LD::ld_again(fin + sbase[pi.A] + ad.z);
-            vb = LD::ld_again(fin + sbase[pi.B] + ad.z);
+            va = LD::ld_again(fin + (sbase[pi.A] + ad.z));   // one 32-bit add, one address add
+            vb = LD::ld_again(fin + (sbase[pi.B] + ad.z));
         }
     }
 };
