@@ -135,6 +135,21 @@ int lbm_row_mean_T(lbm_ctx *c, double *Tbar, int on_device);
  * or the temperatures are not ordered T_u < T_m < T_d.                                */
 int lbm_widths(lbm_ctx *c, double T_u, double T_m, double T_d, double out[2], double *dL_dTbar);
 
+/* Tent-map mixing widths of the two fronts, Eq. (3L) of Sec. IV:
+ *   L_u = sum_z Theta[(Tbar(z) - T_u) / (T_m - T_u)],  L_d = sum_z Theta[(Tbar(z) - T_m) / (T_d - T_m)],
+ * with Theta[b] = 2 b on (0, 1/2), 2 (1 - b) on [1/2, 1) and 0 elsewhere, Tbar the horizontal
+ * mean of the raw T (lbm_row_mean_T), the integral over z taken as the sum over rows (in
+ * sites).  For a single front pass a virtual T_m between T_u and T_d.  Host out[2] =
+ * {L_u, L_d}.  Synchronises.  LBM_EINVAL unless T_u < T_m < T_d.                       */
+int lbm_tent_widths(lbm_ctx *c, double T_u, double T_m, double T_d, double out[2]);
+
+/* Per-row statistics over x of the current state (the fluctuation profiles of Sec. IV):
+ * mean and rms fluctuation sqrt(<(q - <q>_x)^2>_x) of q = T (raw) and of q = E_k, the
+ * kinetic energy per unit mass |u^H|^2 / 2 with u^H the renormalised velocity.  Two
+ * passes (means, then squared deviations), FP64, fixed summation order.  Each output is
+ * an array of Lz doubles or NULL to skip; on_device as for lbm_get_populations.        */
+int lbm_row_stats(lbm_ctx *c, double *T_mean, double *T_rms, double *Ek_mean, double *Ek_rms, int on_device);
+
 /* Total mass sum f and energy sum |xi|^2 f / 2 of the current state, reduced in FP64
  * in a fixed order (host out[2]).  Synchronises; LBM_ENUMERIC if either is not
  * finite.                                                                             */

@@ -161,6 +161,84 @@ __global__ void k_rowT_final(const double* __restrict__ part, int nchunk, int Lx
     Tbar[z] = s / (double)Lx;
 }
 
+// Per-row statistics over x (Sec. IV fluctuation profiles) of T and of the kinetic energy
+// per unit mass E_k = |u^H|^2 / 2 (u^H = u - gvec/2, the renormalised velocity), in two
+// passes over columns chunked like k_rowT_partial: mean == nullptr sums q; otherwise
+// sums (q - mean)^2 with mean[0..Lz) for T and mean[Lz..2 Lz) for E_k.
+// part[(c * 2 + k) * Lz + z], k = 0 (T), 1 (E_k).
+template <class S>
+__global__ void k_row_stats_partial(const typename S::T* __restrict__ f, int Lx, int Lz, int nx_per,
+                                    double grav, const double* __restrict__ mean, double* __restrict__ part) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (z >= Lz) return;
+    const int x0 = c * nx_per, x1 = min(Lx, x0 + nx_per);
+    double a = 0.0, b = 0.0;
+    for (int x = x0; x < x1; x++) {
+        double R, U, V, TT;
+        site_moments<S>(f, x, z, Lz, Lx * Lz, R, U, V, TT);
+        const double vh = V + 0.5 * grav;
+        const double ek = 0.5 * (U * U + vh * vh);
+        if (mean) {
+            const double dt = TT - mean[z], de = ek - mean[Lz + z];
+            a += dt * dt;
+            b += de * de;
+        } else {
+            a += TT;
+            b += ek;
+        }
+    }
+    part[(2 * c) * Lz + z] = a;
+    part[(2 * c + 1) * Lz + z] = b;
+}
+
+// Stage 2: out[k * Lz + z] = (sum_c part[c][k][z]) / Lx, chunks added in order; the
+// square root of it when root != 0 (rms of the deviations).
+__global__ void k_row_stats_final(const double* __restrict__ part, int nchunk, int Lx, int Lz, int root,
+                                  double* __restrict__ out) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= Lz) return;
+    for (int k = 0; k < 2; k++) {
+        double s = 0.0;
+        for (int c = 0; c < nchunk; c++) s += part[(2 * c + k) * Lz + z];
+        s /= (double)Lx;
+        out[k * Lz + z] = root ? sqrt(s) : s;
+    }
+}
+
+// Tent-map widths, Eq. (3L): L_u = sum_z Theta[(Tbar - T_u)/(T_m - T_u)],
+// L_d = sum_z Theta[(Tbar - T_m)/(T_d - T_m)] with Theta[b] = 2b on (0, 1/2),
+// 2 (1 - b) on [1/2, 1), 0 elsewhere.  One block, fixed-order tree sum.
+__device__ __forceinline__ double tent_map(double b) {
+    if (b > 0.0 && b < 0.5) return 2.0 * b;
+    if (b >= 0.5 && b < 1.0) return 2.0 * (1.0 - b);
+    return 0.0;
+}
+
+__global__ void __launch_bounds__(256)
+k_tent_widths(const double* __restrict__ Tbar, int Lz, double Tu, double Tm, double Td, double* __restrict__ out) {
+    __shared__ double sm[2][256];
+    double a = 0.0, b = 0.0;
+    for (int z = threadIdx.x; z < Lz; z += 256) {
+        a += tent_map((Tbar[z] - Tu) / (Tm - Tu));
+        b += tent_map((Tbar[z] - Tm) / (Td - Tm));
+    }
+    sm[0][threadIdx.x] = a;
+    sm[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + w];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sm[0][0];
+        out[1] = sm[1][0];
+    }
+}
+
 // Global mass and energy: per-block partial sums (fixed order), then one final block.
 constexpr int RED_THREADS = 256;
 

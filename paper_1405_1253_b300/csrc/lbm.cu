@@ -499,6 +499,58 @@ int lbm_row_mean_T(lbm_ctx* c, double* Tbar, int on_device) {
     return LBM_OK;
 }
 
+int lbm_tent_widths(lbm_ctx* c, double T_u, double T_m, double T_d, double out[2]) {
+    if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
+    if (!(T_u < T_m && T_m < T_d)) return fail(LBM_EINVAL, "need T_u < T_m < T_d");
+    DeviceGuard dg(c->device);
+    int rc = row_mean_device(c, c->small);
+    if (rc) return rc;
+    double* res = c->small + c->Lz;
+    k_tent_widths<<<1, 256, 0, c->stream>>>(c->small, c->Lz, T_u, T_m, T_d, res);
+    LAUNCH_CHECK();
+    CU(cudaMemcpyAsync(out, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_row_stats(lbm_ctx* c, double* T_mean, double* T_rms, double* Ek_mean, double* Ek_rms, int on_device) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!T_mean && !T_rms && !Ek_mean && !Ek_rms) return LBM_OK;
+    DeviceGuard dg(c->device);
+    const int Lz = c->Lz;
+    const int target = std::max(1, (148 * 16 * 128) / std::max(1, Lz));
+    const int nx_per = (c->Lx + std::min(c->Lx, target) - 1) / std::min(c->Lx, target);
+    const int nch = (c->Lx + nx_per - 1) / nx_per;
+    // part: 2 * nch * Lz partial sums, then 4 * Lz results (means, rms)
+    int rc = ensure_part(c, (size_t)(2 * nch + 4) * Lz);
+    if (rc) return rc;
+    double* means = c->part + (size_t)2 * nch * Lz;
+    double* rms = means + 2 * (size_t)Lz;
+    dim3 grid((Lz + 127) / 128, nch);
+    const void* f = c->buf[c->cur];
+    for (int pass = 0; pass < 2; pass++) {
+        const double* m = pass ? means : nullptr;
+        switch (c->prec) {
+            case LBM_F64: case LBM_F64_FF:
+                k_row_stats_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, Lz, nx_per, c->grav, m, c->part);
+                break;
+            default:
+                k_row_stats_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, c->Lx, Lz, nx_per, c->grav, m, c->part);
+                break;
+        }
+        LAUNCH_CHECK();
+        k_row_stats_final<<<(Lz + 127) / 128, 128, 0, c->stream>>>(c->part, nch, c->Lx, Lz, pass, pass ? rms : means);
+        LAUNCH_CHECK();
+    }
+    const double* src[4] = {means, rms, means + Lz, rms + Lz};
+    double* dst[4] = {T_mean, T_rms, Ek_mean, Ek_rms};
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int i = 0; i < 4; i++)
+        if (dst[i]) CU(cudaMemcpyAsync(dst[i], src[i], (size_t)Lz * sizeof(double), kind, c->stream));
+    if (!on_device) CU(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
 int lbm_widths(lbm_ctx* c, double T_u, double T_m, double T_d, double out[2], double* dL_dTbar) {
     if (!c || !out) return fail(LBM_EINVAL, "NULL argument");
     if (!(T_u < T_m && T_m < T_d)) return fail(LBM_EINVAL, "need T_u < T_m < T_d");

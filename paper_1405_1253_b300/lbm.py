@@ -47,6 +47,8 @@ _SIGS = {
     "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i]),
     "lbm_row_mean_T": (_i, [_vp, _vp, _i]),
     "lbm_widths": (_i, [_vp, _d, _d, _d, _dp, _dp]),
+    "lbm_tent_widths": (_i, [_vp, _d, _d, _d, _dp]),
+    "lbm_row_stats": (_i, [_vp, _dp, _dp, _dp, _dp, _i]),
     "lbm_global_sums": (_i, [_vp, _dp]),
     "lbm_adjoint_step": (_i, [_vp, _vp, _vp, _vp]),
     "lbm_loss_adjoint": (_i, [_vp, _vp, _dp, _vp]),
@@ -212,6 +214,18 @@ class Lattice:
         _check(_lib.lbm_widths(self.ctx, float(T_u), float(T_m), float(T_d), _dptr(out),
                                _dptr(dL) if with_grad else None))
         return (out, dL) if with_grad else out
+
+    def tent_widths(self, T_u, T_m, T_d) -> np.ndarray:
+        """(L_u, L_d) by the tent-map integral of Eq. (3L), in sites."""
+        out = np.zeros(2)
+        _check(_lib.lbm_tent_widths(self.ctx, float(T_u), float(T_m), float(T_d), _dptr(out)))
+        return out
+
+    def row_stats(self) -> dict:
+        """Per-row mean and rms fluctuation over x of T and of E_k = |u^H|^2 / 2."""
+        outs = {k: np.empty(self.Lz) for k in ("T_mean", "T_rms", "Ek_mean", "Ek_rms")}
+        _check(_lib.lbm_row_stats(self.ctx, *[_dptr(outs[k]) for k in ("T_mean", "T_rms", "Ek_mean", "Ek_rms")], 0))
+        return outs
 
     def global_sums(self) -> np.ndarray:
         out = np.zeros(2)

@@ -59,14 +59,16 @@ class Lattice:
     T_d: float = T_D
     rho_ref: float = RHO_REF
     tanh_w: float = TANH_W
+    z_lo_rows: float | None = None   # unperturbed interface heights in sites (default Lz/3, 2 Lz/3)
+    z_hi_rows: float | None = None
 
     @property
     def z_lo(self) -> float:
-        return self.Lz / 3.0
+        return self.Lz / 3.0 if self.z_lo_rows is None else self.z_lo_rows
 
     @property
     def z_hi(self) -> float:
-        return 2.0 * self.Lz / 3.0
+        return 2.0 * self.Lz / 3.0 if self.z_hi_rows is None else self.z_hi_rows
 
     @property
     def sites(self) -> int:
@@ -94,6 +96,25 @@ GRADIENT_256x512 = Lattice(256, 512, tau=0.8, grav=1e-4, K=16, sigma=1.0, seed=5
 GRADIENT_STEPS = 2000
 GRADIENT_CKPT = 100
 ENSEMBLE_STEPS = 3000
+
+
+def fronts(case: str, seed: int, Lx: int = 384, Lz: int = 1024, tau: float = 0.6) -> Lattice:
+    """Table II's two cases scaled to Lx x Lz (aspect ~ 2400:6144), Atwood number 0.025:
+    T_u = 0.975, T_d = 1.025; "double": a middle layer at T_m = 1 of depth Lz/12 centred at
+    Lz/2; "single": T_u above Lz/2, T_d below (T_m = T_u, no second jump).  Gravity keeps the
+    adiabatic length 2 (T_d - T_u) / g at ~1.085 Lz as in Table II; white-noise interfaces of
+    K = Lx/2 modes with an rms displacement of one site."""
+    K = Lx // 2
+    g = 2.0 * 0.05 / (1.085 * Lz)
+    sigma = float(np.sqrt(2.0 / K))
+    if case == "double":
+        d = Lz / 12.0
+        return Lattice(Lx, Lz, tau=tau, grav=g, K=K, sigma=sigma, seed=seed, T_u=0.975, T_m=1.0, T_d=1.025,
+                       z_lo_rows=Lz / 2.0 - d / 2.0, z_hi_rows=Lz / 2.0 + d / 2.0)
+    if case == "single":
+        return Lattice(Lx, Lz, tau=tau, grav=g, K=K, sigma=sigma, seed=seed, T_u=0.975, T_m=0.975, T_d=1.025,
+                       z_lo_rows=Lz / 2.0, z_hi_rows=float(Lz))
+    raise ValueError(case)
 
 
 def ensemble_48() -> list[Lattice]:
