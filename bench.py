@@ -273,6 +273,34 @@ def bench_adjoint(torch):
             "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
 
 
+def bench_slabs(torch, lbm, lat, steps, stream, prec="f64_ff"):
+    """The x-slab decomposition of Sec. III.B on this device (halos exchanged by device
+    copies each step): MLUPS for 1, 4 and 8 slabs with the exchange overlapped with the
+    bulk update, and 8 slabs without overlap, against the single-domain step."""
+    def timed(fn):
+        fn(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+    L.init_from(lat)
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, {prec}, {steps} steps", "single_ms": timed(L.step)}
+    for n, ov in ((1, True), (4, True), (8, True), (8, False)):
+        S = lbm.Slabs(L, n)
+        S.scatter()
+        ms = timed(lambda k: S.step(k, ov))
+        S.close()
+        key = f"{n}_slabs" + ("" if ov else "_no_overlap")
+        out[key] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6,
+                    "halo_bytes_per_step": 2 * n * 3 * lat.Lz * 37 * lbm.POP_BYTES[prec]}
+    L.close()
+    return out
+
+
 def fp32_error(torch, lbm, lat, steps, stream):
     """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
     step after `steps` steps from the same initial state."""
@@ -359,6 +387,7 @@ def run_ours(args):
         extras["ensemble_f64"] = bench_ensemble(torch, lbm, "f64_ff", 100, es)
         extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", 100, es)
         extras["adjoint"] = bench_adjoint(torch)
+        extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
 
     if rank != 0:
         return
@@ -410,7 +439,7 @@ def main():
     ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip ensemble, adjoint and FP32-error sections")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, adjoint, slab and FP32-error sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -243,6 +243,33 @@ int lbm_ensemble_set_wait(lbm_ensemble *e, long long spin_limit_cycles, unsigned
  * make it before any stream capture.  Calls no cudaMalloc/cudaFree.  Asynchronous.    */
 int lbm_row_mean_T_noalloc(const double *f, int Lx, int Lz, double *Tbar, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+ * x-slab decomposition (Sec. III.B: the lattice split along x into slabs of Lx/nslab
+ * columns, each with H_x = 3 halo columns per side refreshed from its neighbours before
+ * every step), run on the device of one context.  The slabs live in library-owned buffers
+ * (2 copies of nslab * 37 * (Lx/nslab + 6) * Lz populations).  Results equal lbm_step's
+ * bit for bit.
+ * ------------------------------------------------------------------------------- */
+typedef struct lbm_slabs lbm_slabs;   /* opaque */
+
+/* Slabs for the lattice of c.  LBM_EINVAL unless nslab divides Lx with at least 3
+ * columns per slab; LBM_ENOMEM if the buffers cannot be allocated.                    */
+int lbm_slabs_create(lbm_slabs **out, lbm_ctx *c, int nslab);
+int lbm_slabs_destroy(lbm_slabs *s);
+
+/* Copy the context's current state into the slabs (asynchronous, c's stream).         */
+int lbm_slabs_scatter(lbm_slabs *s);
+
+/* nsteps steps of every slab: halo exchange by device copies, then the step kernel on
+ * each slab's own columns.  overlap = 1 (and slabs wider than 6 columns): the columns that
+ * need no halo run on a second stream while the exchange and the edge columns run on c's
+ * stream, the paper's overlap of communication with the bulk update; 0: exchange, then
+ * whole slabs, all on c's stream.  Asynchronous with respect to the host.             */
+int lbm_slabs_step(lbm_slabs *s, int nsteps, int overlap);
+
+/* Copy the slabs' state back into the context's current buffer; synchronises.       */
+int lbm_slabs_gather(lbm_slabs *s);
+
 /* Message of the last failed call on this thread ("" if none).                        */
 const char *lbm_last_error(void);
 

@@ -63,20 +63,23 @@ __device__ __forceinline__ int pull_index_interior(int z, const int col[7], int 
     return L * plane + col[3 - cx(L)] + z - cz(L);
 }
 
-// Tiling of one step launch (1D grid of BLOCK_Z-thread tiles):
+// Tiling of one step launch over the columns [x0, x0 + nx) (1D grid of block-thread tiles):
 //   blocks [0, nwall):        wall tiles, one thread per (x, row) over the six rows
 //                             0, 1, 2, Lz-3, Lz-2, Lz-1 (half-way bounce-back applies);
-//   blocks [nwall, nwall + nzb * Lx): interior tiles, column x, rows zb*BLOCK_Z + t, aligned
+//   blocks [nwall, nwall + nzb * nx): interior tiles, column x, rows zb*block + t, aligned
 //                             to row 0 so warps store whole sectors; threads outside
 //                             3 <= z < Lz - 3 return (no wall test in this path).
-// Wall tiles come first so their scattered loads overlap with the interior work.
+// Wall tiles come first so their scattered loads overlap with the interior work.  A whole
+// lattice is x0 = 0, nx = Lx; a column range serves the x-slab decomposition (slabs.cuh).
 struct Tiling {
     int nwall, nzb;
+    int x0, nx;
 };
-inline Tiling make_tiling(int Lx, int Lz, int block) {
-    return Tiling{(6 * Lx + block - 1) / block, (Lz + block - 1) / block};
+inline Tiling make_tiling_cols(int x0, int nx, int Lz, int block) {
+    return Tiling{(6 * nx + block - 1) / block, (Lz + block - 1) / block, x0, nx};
 }
-inline int tiling_blocks(const Tiling& t, int Lx) { return t.nwall + t.nzb * Lx; }
+inline Tiling make_tiling(int Lx, int Lz, int block) { return make_tiling_cols(0, Lx, Lz, block); }
+inline int tiling_blocks(const Tiling& t) { return t.nwall + t.nzb * t.nx; }
 
 struct SiteAddr {
     int x, z, Lz, plane, Lx;
@@ -89,14 +92,16 @@ struct SiteAddr {
         wall = b < t.nwall;
         if (wall) {
             const int i = b * blockDim.x + threadIdx.x;
-            if (i >= 6 * Lx) return false;
-            x = i / 6;
-            const int r = i - 6 * x;
+            if (i >= 6 * t.nx) return false;
+            const int xi = i / 6;
+            const int r = i - 6 * xi;
+            x = t.x0 + xi;
             z = r < 3 ? r : Lz - 6 + r;
         } else {
             const int tt = b - t.nwall;
-            x = tt / t.nzb;
-            z = (tt - x * t.nzb) * blockDim.x + threadIdx.x;
+            const int xi = tt / t.nzb;
+            x = t.x0 + xi;
+            z = (tt - xi * t.nzb) * blockDim.x + threadIdx.x;
             if (z < 3 || z >= Lz - 3) return false;
         }
 #pragma unroll
@@ -127,7 +132,7 @@ struct SiteAddr {
 // Block-uniform decomposition of a tile: wall flag, and for interior tiles the column x
 // and the first row.  Every thread of the block computes the same values.
 __device__ __forceinline__ bool tile_is_wall(Tiling t, int b) { return b < t.nwall; }
-__device__ __forceinline__ int tile_column(Tiling t, int b) { return (b - t.nwall) / t.nzb; }
+__device__ __forceinline__ int tile_column(Tiling t, int b) { return t.x0 + (b - t.nwall) / t.nzb; }
 
 // Load policies.  LoadNC: read-only path (populations written by an earlier launch).
 // LoadCG: L2-coherent loads, for data written earlier in the same launch by other CTAs

@@ -197,6 +197,16 @@ static void free_ctx(lbm_ctx* c) {
     delete c;
 }
 
+// One step of the columns of tiling t in precision prec (p describes the buffers).
+static void launch_step(int prec, const void* fin, void* fout, const StepParams& p, const Tiling& t,
+                        cudaStream_t st) {
+    switch (prec) {
+        case LBM_F64: launch_step_f64((const double*)fin, (double*)fout, p, t, st); break;
+        case LBM_F64_FF: launch_step_ff((const double*)fin, (double*)fout, p, quad_w_shell(), t, st); break;
+        default: launch_step_f32((const float*)fin, (float*)fout, p, t, st); break;
+    }
+}
+
 template <class S>
 static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renorm) {
     dim3 grid((c->Lz + 127) / 128, c->Lx);
@@ -360,20 +370,9 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     for (int s = 0; s < nsteps; s++) {
-        void* fin = c->buf[c->cur];
-        void* fout = c->buf[c->cur ^ 1];
-        switch (c->prec) {
-            case LBM_F64:
-                launch_step_f64((const double*)fin, (double*)fout, p, c->stream);
-                break;
-            case LBM_F64_FF:
-                launch_step_ff((const double*)fin, (double*)fout, p, quad_w_shell(), c->stream);
-                break;
-            default:
-                launch_step_f32((const float*)fin, (float*)fout, p, c->stream);
-                break;
-        }
+        launch_step(c->prec, c->buf[c->cur], c->buf[c->cur ^ 1], p, t, c->stream);
         LAUNCH_CHECK();
         c->cur ^= 1;
     }
@@ -680,7 +679,7 @@ static int ens_layout(lbm_ensemble* e) {
         L.cur = c->cur;
         L.t = make_tiling(c->Lx, c->Lz, e->tz);
         L.tile_begin = tb;
-        L.ntiles = tiling_blocks(L.t, c->Lx);
+        L.ntiles = tiling_blocks(L.t);
         tb += L.ntiles;
     }
     e->total_tiles = tb;
@@ -993,3 +992,185 @@ extern "C" int lbm_row_mean_T_noalloc(const double* f, int Lx, int Lz, double* T
     LAUNCH_CHECK();
     return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// x-slab decomposition of Sec. III.B (the paper's multi-GPU layout) on one device.
+// Slab k owns the global columns [k Lxs, (k + 1) Lxs) and keeps them at local columns
+// [HX, HX + Lxs) of a buffer of W = Lxs + 2 HX columns; local columns [0, HX) and
+// [HX + Lxs, W) are halos holding the neighbours' edge columns (periodic in k), refreshed
+// before every step, so the step kernels never wrap x inside a slab.
+// Overlap mode (the paper's three-stream scheme): the bulk columns [2 HX, Lxs) need no
+// halo and run on a second stream while the halo copies and then the edge columns
+// [HX, 2 HX) and [Lxs, Lxs + HX) run on the context's stream.  Per step t (input B_t):
+//   bulk stream: wait ev_comm[t-1]; bulk kernels;                   record ev_bulk[t]
+//   comm stream: wait ev_bulk[t-1]; halo copies into B_t; edges;    record ev_comm[t]
+// bulk(t) reads interior columns of B_t written by bulk(t-1) (same stream) and edge(t-1)
+// (ev_comm), and writes B_{t+1} = B_{t-1}, which bulk(t-1) and edge(t-1) read; edge(t)
+// reads B_t columns written by bulk(t-1) (ev_bulk) and writes B_{t-1}, read by bulk(t-1).
+// ---------------------------------------------------------------------------------
+namespace {
+constexpr int HX = 3;   // halo columns = max |c_x|
+}
+
+struct lbm_slabs {
+    lbm_ctx* c = nullptr;
+    int n = 0, Lxs = 0, W = 0;
+    size_t es = 0, slab_elems = 0;     // element size, Q * W * Lz elements per slab copy
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaStream_t bulk = nullptr;
+    cudaEvent_t ev_bulk[2] = {nullptr, nullptr}, ev_comm[2] = {nullptr, nullptr};
+    long long t = 0;                   // steps taken (event parity)
+};
+
+static void slabs_free(lbm_slabs* s) {
+    for (int i = 0; i < 2; i++) {
+        if (s->buf[i]) cudaFree(s->buf[i]);
+        if (s->ev_bulk[i]) cudaEventDestroy(s->ev_bulk[i]);
+        if (s->ev_comm[i]) cudaEventDestroy(s->ev_comm[i]);
+    }
+    if (s->bulk) cudaStreamDestroy(s->bulk);
+    delete s;
+}
+
+static char* slab_base(const lbm_slabs* s, int b, int k) {
+    return (char*)s->buf[b] + (size_t)k * s->slab_elems * s->es;
+}
+
+// Halo columns of every slab of copy b from its neighbours' edge columns, on stream st.
+static int slabs_exchange(lbm_slabs* s, int b, cudaStream_t st) {
+    const size_t Lz = s->c->Lz;
+    const size_t pitch = (size_t)s->W * Lz * s->es, width = (size_t)HX * Lz * s->es;
+    for (int k = 0; k < s->n; k++) {
+        const int km = (k + s->n - 1) % s->n, kp = (k + 1) % s->n;
+        CU(cudaMemcpy2DAsync(slab_base(s, b, k), pitch, slab_base(s, b, km) + (size_t)s->Lxs * Lz * s->es, pitch,
+                             width, Q, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpy2DAsync(slab_base(s, b, k) + (size_t)(HX + s->Lxs) * Lz * s->es, pitch,
+                             slab_base(s, b, kp) + (size_t)HX * Lz * s->es, pitch, width, Q,
+                             cudaMemcpyDeviceToDevice, st));
+    }
+    return LBM_OK;
+}
+
+// Interior columns between the context's current copy and the slabs' copy cur.
+static int slabs_copy_interiors(lbm_slabs* s, bool to_slabs) {
+    lbm_ctx* c = s->c;
+    const size_t Lz = c->Lz;
+    const size_t gpitch = (size_t)c->Lx * Lz * s->es, spitch = (size_t)s->W * Lz * s->es;
+    const size_t width = (size_t)s->Lxs * Lz * s->es;
+    for (int k = 0; k < s->n; k++) {
+        char* g = (char*)c->buf[c->cur] + (size_t)k * s->Lxs * Lz * s->es;
+        char* l = slab_base(s, s->cur, k) + (size_t)HX * Lz * s->es;
+        if (to_slabs) CU(cudaMemcpy2DAsync(l, spitch, g, gpitch, width, Q, cudaMemcpyDeviceToDevice, c->stream));
+        else CU(cudaMemcpy2DAsync(g, gpitch, l, spitch, width, Q, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_slabs_create(lbm_slabs** out, lbm_ctx* c, int nslab) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (nslab < 1 || c->Lx % nslab) return fail(LBM_EINVAL, "Lx = %d is not a multiple of nslab = %d", c->Lx, nslab);
+    if (c->Lx / nslab < HX) return fail(LBM_EINVAL, "slabs of %d columns: need at least %d", c->Lx / nslab, HX);
+    DeviceGuard dg(c->device);
+    lbm_slabs* s = new lbm_slabs();
+    s->c = c;
+    s->n = nslab;
+    s->Lxs = c->Lx / nslab;
+    s->W = s->Lxs + 2 * HX;
+    s->es = pop_bytes(c->prec);
+    s->slab_elems = (size_t)Q * s->W * c->Lz;
+    bool ok = (long long)s->slab_elems < (1LL << 31);
+    for (int i = 0; ok && i < 2; i++)
+        ok = cudaMalloc(&s->buf[i], (size_t)nslab * s->slab_elems * s->es) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->ev_bulk[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->ev_comm[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->bulk, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        slabs_free(s);
+        return fail(LBM_ENOMEM, "slab buffers or streams could not be created");
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+int lbm_slabs_destroy(lbm_slabs* s) {
+    if (!s) return LBM_OK;
+    DeviceGuard dg(s->c->device);
+    cudaStreamSynchronize(s->c->stream);
+    cudaStreamSynchronize(s->bulk);
+    slabs_free(s);
+    return LBM_OK;
+}
+
+int lbm_slabs_scatter(lbm_slabs* s) {
+    if (!s) return fail(LBM_EINVAL, "slabs is NULL");
+    DeviceGuard dg(s->c->device);
+    int rc = slabs_copy_interiors(s, true);
+    if (rc) return rc;
+    s->t = 0;
+    return LBM_OK;
+}
+
+int lbm_slabs_step(lbm_slabs* s, int nsteps, int overlap) {
+    if (!s) return fail(LBM_EINVAL, "slabs is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    lbm_ctx* c = s->c;
+    DeviceGuard dg(c->device);
+    StepParams p = step_params(c);
+    p.Lx = s->W;                      // the kernels address one slab buffer
+    p.plane = s->W * c->Lz;
+    const bool ov = overlap && s->Lxs > 2 * HX;
+    const Tiling whole = make_tiling_cols(HX, s->Lxs, c->Lz, BLOCK_Z);
+    const Tiling bulk = make_tiling_cols(2 * HX, s->Lxs - 2 * HX, c->Lz, BLOCK_Z);
+    const Tiling edge_lo = make_tiling_cols(HX, HX, c->Lz, BLOCK_Z);
+    const Tiling edge_hi = make_tiling_cols(s->Lxs, HX, c->Lz, BLOCK_Z);
+    if (ov && s->t == 0) {            // first step: both streams start after the scatter
+        CU(cudaEventRecord(s->ev_comm[1], c->stream));
+        CU(cudaEventRecord(s->ev_bulk[1], c->stream));
+    }
+    for (int i = 0; i < nsteps; i++) {
+        const int b = s->cur;
+        if (!ov) {
+            int rc = slabs_exchange(s, b, c->stream);
+            if (rc) return rc;
+            for (int k = 0; k < s->n; k++)
+                launch_step(c->prec, slab_base(s, b, k), slab_base(s, b ^ 1, k), p, whole, c->stream);
+            LAUNCH_CHECK();
+        } else {
+            const int now = (int)(s->t & 1), prev = now ^ 1;
+            CU(cudaStreamWaitEvent(s->bulk, s->ev_comm[prev], 0));
+            for (int k = 0; k < s->n; k++)
+                launch_step(c->prec, slab_base(s, b, k), slab_base(s, b ^ 1, k), p, bulk, s->bulk);
+            LAUNCH_CHECK();
+            CU(cudaEventRecord(s->ev_bulk[now], s->bulk));
+            CU(cudaStreamWaitEvent(c->stream, s->ev_bulk[prev], 0));
+            int rc = slabs_exchange(s, b, c->stream);
+            if (rc) return rc;
+            for (int k = 0; k < s->n; k++) {
+                launch_step(c->prec, slab_base(s, b, k), slab_base(s, b ^ 1, k), p, edge_lo, c->stream);
+                launch_step(c->prec, slab_base(s, b, k), slab_base(s, b ^ 1, k), p, edge_hi, c->stream);
+            }
+            LAUNCH_CHECK();
+            CU(cudaEventRecord(s->ev_comm[now], c->stream));
+        }
+        s->cur ^= 1;
+        s->t++;
+    }
+    if (ov && nsteps > 0) CU(cudaStreamWaitEvent(c->stream, s->ev_bulk[(s->t - 1) & 1], 0));
+    return LBM_OK;
+}
+
+int lbm_slabs_gather(lbm_slabs* s) {
+    if (!s) return fail(LBM_EINVAL, "slabs is NULL");
+    DeviceGuard dg(s->c->device);
+    int rc = slabs_copy_interiors(s, false);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(s->c->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -151,10 +151,10 @@ inline StepParamsF f32_params(const StepParams& p) {
     return q;
 }
 
-inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, cudaStream_t st) {
+// One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
+inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, const Tiling& t, cudaStream_t st) {
     const StepParamsF q = f32_params(p);
-    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
-    k_step_f32<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
+    k_step_f32<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 }  // namespace lbm

@@ -105,9 +105,9 @@ k_step_f64(const double* __restrict__ fin, double* __restrict__ fout, StepParams
     tile_f64<LoadNC>(fin, fout, p, t, blockIdx.x);
 }
 
-inline void launch_step_f64(const double* fin, double* fout, const StepParams& p, cudaStream_t st) {
-    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
-    k_step_f64<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, p, t);
+// One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
+inline void launch_step_f64(const double* fin, double* fout, const StepParams& p, const Tiling& t, cudaStream_t st) {
+    k_step_f64<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, p, t);
 }
 
 }  // namespace lbm

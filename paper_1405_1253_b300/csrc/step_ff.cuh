@@ -227,11 +227,11 @@ inline StepParamsFF ff_params(const StepParams& p, const double* w_shell) {
     return q;
 }
 
+// One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
 inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, const double* w_shell,
-                           cudaStream_t st) {
+                           const Tiling& t, cudaStream_t st) {
     const StepParamsFF q = ff_params(p, w_shell);
-    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
-    k_step_ff<<<tiling_blocks(t, p.Lx), BLOCK_Z, 0, st>>>(fin, fout, q, t);
+    k_step_ff<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 

@@ -65,6 +65,11 @@ _SIGS = {
     "lbm_ensemble_graph_launch": (_i, [_vp]),
     "lbm_ensemble_sync": (_i, [_vp]),
     "lbm_ensemble_set_wait": (_i, [_vp, ctypes.c_longlong, ctypes.c_uint]),
+    "lbm_slabs_create": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+    "lbm_slabs_destroy": (_i, [_vp]),
+    "lbm_slabs_scatter": (_i, [_vp]),
+    "lbm_slabs_step": (_i, [_vp, _i, _i]),
+    "lbm_slabs_gather": (_i, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -290,6 +295,37 @@ class Ensemble:
         if getattr(self, "e", None):
             _lib.lbm_ensemble_destroy(self.e)
             self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Slabs:
+    """The lattice of `lattice` split into `n` x-slabs with halo exchange (Sec. III.B),
+    emulating the paper's multi-GPU layout on this device."""
+
+    def __init__(self, lattice: Lattice, n: int):
+        self.lattice = lattice
+        s = _vp()
+        _check(_lib.lbm_slabs_create(ctypes.byref(s), lattice.ctx, int(n)))
+        self.s = s
+
+    def scatter(self):
+        _check(_lib.lbm_slabs_scatter(self.s))
+
+    def step(self, n: int = 1, overlap: bool = True):
+        _check(_lib.lbm_slabs_step(self.s, int(n), int(bool(overlap))))
+
+    def gather(self):
+        _check(_lib.lbm_slabs_gather(self.s))
+
+    def close(self):
+        if getattr(self, "s", None):
+            _lib.lbm_slabs_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:
