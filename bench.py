@@ -301,6 +301,30 @@ def bench_slabs(torch, lbm, lat, steps, stream, prec="f64_ff"):
     return out
 
 
+def bench_push(torch, lbm, lat, steps, stream):
+    """Pull form (lbm_step: misaligned reads, aligned writes) against the push form
+    (lbm_step_push: aligned reads, misaligned writes), Sec. III.B."""
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps"}
+    for prec in ("f64_ff", "f32"):
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        res = {}
+        for name, fn in (("pull", L.step), ("push", L.step_push)):
+            fn(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[name] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6}
+        res["pull_over_push"] = res["push"]["ms"] / res["pull"]["ms"]
+        out[prec] = res
+        L.close()
+    return out
+
+
 def fp32_error(torch, lbm, lat, steps, stream):
     """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
     step after `steps` steps from the same initial state."""
@@ -388,6 +412,7 @@ def run_ours(args):
         extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", 100, es)
         extras["adjoint"] = bench_adjoint(torch)
         extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
+        extras["push_vs_pull"] = bench_push(torch, lbm, lat, 200, stream)
 
     if rank != 0:
         return
@@ -439,7 +464,7 @@ def main():
     ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, adjoint, slab and FP32-error sections")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, adjoint, slab, push and FP32-error sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -104,6 +104,19 @@ int lbm_init_layers(lbm_ctx *c, const lbm_layers_desc *d);
  * kernel launch per step, ping-ponging between the two buffers.  Asynchronous.       */
 int lbm_step(lbm_ctx *c, int nsteps);
 
+/* Push form of the step (Sec. III.B compares "push" and "pull"; lbm_step is the pull form,
+ * whose stored state is post-collision, f <- C(P f)).  lbm_step_push advances a state
+ * stored post-propagation (pre-collision), g <- P(C g): every site reads its own
+ * populations (aligned) and writes each result at the site it moves to (misaligned), the
+ * wall rule mirrored.  Same collide arithmetic as lbm_step in every precision.
+ * Asynchronous.                                                                       */
+int lbm_step_push(lbm_ctx *c, int nsteps);
+
+/* One propagate + bc without collide, f <- P f (the pull gather).  It maps a pull-form
+ * state to the matching push-form one: push steps from P f equal P applied to the pull
+ * steps from f.  Asynchronous.                                                        */
+int lbm_propagate(lbm_ctx *c);
+
 /* Device address of the buffer holding the current state (buf0 or buf1); NULL for a
  * NULL context.                                                                       */
 void *lbm_current(lbm_ctx *c);

@@ -127,6 +127,33 @@ struct SiteAddr {
         return l * plane + xs * Lz + zs;
     }
     __device__ __forceinline__ int dst() const { return x * Lz + z; }
+    // Push form (collide, then move): the element population L leaving this site is
+    // written to.  The inverse of the pull map: interior (L, x + c_x, z + c_z); a
+    // population that would leave through a wall lands reversed on the same column,
+    // opp(L) at row -c_z - 1 - z (bottom) or 2 Lz - 1 - z - c_z (top).
+    template <int L, bool WALL>
+    __device__ __forceinline__ int push_dst() const {
+        constexpr int CX = cx(L), CZ = cz(L), OP = opp(L);
+        const int zd = z + CZ;
+        if (WALL) {
+            if (CZ < 0 && zd < 0) return OP * plane + x * Lz + (-CZ - 1 - z);
+            if (CZ > 0 && zd >= Lz) return OP * plane + x * Lz + (2 * Lz - 1 - z - CZ);
+        }
+        return L * plane + col[3 + CX] + zd;
+    }
+    // Runtime-velocity form of push_dst() (population l with lattice vector (vx, vz)).
+    template <bool WALL>
+    __device__ __forceinline__ int push_dst_rt(int l, int lop, int vx, int vz) const {
+        const int zd = z + vz;
+        if (WALL) {
+            if (zd < 0) return lop * plane + x * Lz + (-vz - 1 - z);
+            if (zd >= Lz) return lop * plane + x * Lz + (2 * Lz - 1 - z - vz);
+        }
+        int xd = x + vx;
+        xd = xd < 0 ? xd + Lx : (xd >= Lx ? xd - Lx : xd);
+        if (Lx < 3) xd = wrap_x(x + vx, Lx);
+        return l * plane + xd * Lz + zd;
+    }
 };
 
 // Block-uniform decomposition of a tile: wall flag, and for interior tiles the column x
@@ -165,6 +192,13 @@ __device__ __forceinline__ void fill_pull_bases(int* sbase, int x, int Lx, int L
         sbase[l] = l * plane + wrap_x(x - d_vel[l][0], Lx) * Lz - d_vel[l][1];
 }
 
+// Interior tiles, push form: pbase[l] = l * plane + wrap(x + c_lx) * Lz + c_lz, so that
+// population l leaving row z is written at pbase[l] + z.
+__device__ __forceinline__ void fill_push_bases(int* pbase, int x, int Lx, int Lz, int plane) {
+    for (int l = threadIdx.x; l < Q; l += blockDim.x)
+        pbase[l] = l * plane + wrap_x(x + d_vel[l][0], Lx) * Lz + d_vel[l][1];
+}
+
 // Compile-time loop: calls f(Tag<L>{}) for L = 0..N-1.
 template <int L>
 struct Tag { static constexpr int value = L; };
@@ -174,6 +208,29 @@ __device__ __forceinline__ void static_for(F&& f) {
     if constexpr (L < N) {
         f(Tag<L>{});
         static_for<N, L + 1>(f);
+    }
+}
+
+// Array-form sites (native FP64 and FP32 collides): the 37 inputs of the site, pulled
+// (PUSH = false) or its own (PUSH = true) ...
+template <bool PUSH, bool WALL, class LD, class T>
+__device__ __forceinline__ void load_site(const T* __restrict__ fin, const SiteAddr& ad, T (&g)[Q]) {
+    if constexpr (PUSH) {
+        const int o = ad.dst();
+        static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + (l.value * ad.plane + o)); });
+    } else {
+        static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
+    }
+}
+// ... and the 37 results, stored at the site (PUSH = false) or where they move to.
+template <bool PUSH, bool WALL, class T>
+__device__ __forceinline__ void store_site(T* __restrict__ fout, const SiteAddr& ad, const T (&fo)[Q]) {
+    if constexpr (PUSH) {
+        static_for<Q>([&](auto l) { fout[ad.template push_dst<decltype(l)::value, WALL>()] = fo[l.value]; });
+    } else {
+        const int o = ad.dst();
+#pragma unroll
+        for (int l = 0; l < Q; l++) fout[l * ad.plane + o] = fo[l];
     }
 }
 

@@ -355,6 +355,20 @@ __global__ void k_widths(const double* __restrict__ Tbar, int Lz, double Tu, dou
     }
 }
 
+// One propagate + bc without collide, fout = P fin (Sec. III.B: the pull gather with the
+// periodic wrap and the wall rule).  It maps a pull-form state (post-collision) to the
+// matching push-form state (post-propagation).
+template <class T>
+__global__ void __launch_bounds__(BLOCK_Z)
+k_propagate(const T* __restrict__ fin, T* __restrict__ fout, int Lx, int Lz, Tiling t) {
+    SiteAddr ad;
+    bool wall;
+    if (!ad.setup(Lx, Lz, Lx * Lz, t, blockIdx.x, wall)) return;
+    const int o = ad.dst();
+    if (wall) static_for<Q>([&](auto l) { fout[l.value * ad.plane + o] = fin[ad.template src<decltype(l)::value, true>()]; });
+    else static_for<Q>([&](auto l) { fout[l.value * ad.plane + o] = fin[ad.template src<decltype(l)::value, false>()]; });
+}
+
 // ---------------------------------------------------------------------------------
 // Storage <-> canonical FP64 conversion of n elements starting at element `first`.
 // ---------------------------------------------------------------------------------

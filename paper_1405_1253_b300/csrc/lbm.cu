@@ -379,6 +379,43 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     return LBM_OK;
 }
 
+int lbm_step_push(lbm_ctx* c, int nsteps) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    for (int s = 0; s < nsteps; s++) {
+        const void* fin = c->buf[c->cur];
+        void* fout = c->buf[c->cur ^ 1];
+        switch (c->prec) {
+            case LBM_F64: launch_step_f64_push((const double*)fin, (double*)fout, p, t, c->stream); break;
+            case LBM_F64_FF:
+                launch_step_ff_push((const double*)fin, (double*)fout, p, quad_w_shell(), t, c->stream);
+                break;
+            default: launch_step_f32_push((const float*)fin, (float*)fout, p, t, c->stream); break;
+        }
+        LAUNCH_CHECK();
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_propagate(lbm_ctx* c) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->device);
+    const Tiling t = make_tiling(c->Lx, c->Lz, BLOCK_Z);
+    const void* fin = c->buf[c->cur];
+    void* fout = c->buf[c->cur ^ 1];
+    if (pop_bytes(c->prec) == 8)
+        k_propagate<double><<<tiling_blocks(t), BLOCK_Z, 0, c->stream>>>((const double*)fin, (double*)fout, c->Lx, c->Lz, t);
+    else
+        k_propagate<float><<<tiling_blocks(t), BLOCK_Z, 0, c->stream>>>((const float*)fin, (float*)fout, c->Lx, c->Lz, t);
+    LAUNCH_CHECK();
+    c->cur ^= 1;
+    return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------------
 // Population copies
 // ---------------------------------------------------------------------------------

@@ -116,30 +116,34 @@ __device__ __forceinline__ void collide_f32(const float (&g)[Q], float (&fo)[Q],
     fo[4] = g[4] + (D1[3] + fmaf(-0.5f, d1z, 0.25f * d2));
 }
 
-template <bool WALL, class LD>
+// One site, pull (PUSH = false) or push (PUSH = true) form (see site_f64).
+template <bool WALL, class LD, bool PUSH>
 __device__ __forceinline__ void site_f32(const float* __restrict__ fin, float* __restrict__ fout,
                                         const SiteAddr& ad, const StepParamsF& p) {
     float g[Q], fo[Q];
-    static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
+    load_site<PUSH, WALL, LD>(fin, ad, g);
     collide_f32(g, fo, p);
-    const int o = ad.dst();
-#pragma unroll
-    for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
+    store_site<PUSH, WALL>(fout, ad, fo);
 }
 
-template <class LD>
+template <class LD, bool PUSH = false>
 __device__ __forceinline__ void tile_f32(const float* __restrict__ fin, float* __restrict__ fout,
                                         const StepParamsF& p, Tiling t, int b) {
     SiteAddr ad;
     bool wall;
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    if (wall) site_f32<true, LD>(fin, fout, ad, p);
-    else site_f32<false, LD>(fin, fout, ad, p);
+    if (wall) site_f32<true, LD, PUSH>(fin, fout, ad, p);
+    else site_f32<false, LD, PUSH>(fin, fout, ad, p);
 }
 
 __global__ void __launch_bounds__(BLOCK_Z)
 k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
     tile_f32<LoadNC>(fin, fout, p, t, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f32_push(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
+    tile_f32<LoadNC, true>(fin, fout, p, t, blockIdx.x);
 }
 
 inline StepParamsF f32_params(const StepParams& p) {
@@ -155,6 +159,11 @@ inline StepParamsF f32_params(const StepParams& p) {
 inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, const Tiling& t, cudaStream_t st) {
     const StepParamsF q = f32_params(p);
     k_step_f32<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
+}
+inline void launch_step_f32_push(const float* fin, float* fout, const StepParams& p, const Tiling& t,
+                                 cudaStream_t st) {
+    const StepParamsF q = f32_params(p);
+    k_step_f32_push<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 }  // namespace lbm

@@ -78,26 +78,26 @@ __device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q
     });
 }
 
-template <bool WALL, class LD>
+// One site: pull form (PUSH = false: gather the pulled populations, store at the site) or
+// push form (PUSH = true: the site's own populations, stored where they move to).
+template <bool WALL, class LD, bool PUSH>
 __device__ __forceinline__ void site_f64(const double* __restrict__ fin, double* __restrict__ fout,
                                         const SiteAddr& ad, const StepParams& p) {
     double g[Q], fo[Q];
-    static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
+    load_site<PUSH, WALL, LD>(fin, ad, g);
     collide_f64(g, fo, p);
-    const int o = ad.dst();
-#pragma unroll
-    for (int l = 0; l < Q; l++) fout[l * p.plane + o] = fo[l];
+    store_site<PUSH, WALL>(fout, ad, fo);
 }
 
 // One BLOCK_Z-thread tile b of the lattice tiling t.
-template <class LD>
+template <class LD, bool PUSH = false>
 __device__ __forceinline__ void tile_f64(const double* __restrict__ fin, double* __restrict__ fout,
                                         const StepParams& p, Tiling t, int b) {
     SiteAddr ad;
     bool wall;
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    if (wall) site_f64<true, LD>(fin, fout, ad, p);
-    else site_f64<false, LD>(fin, fout, ad, p);
+    if (wall) site_f64<true, LD, PUSH>(fin, fout, ad, p);
+    else site_f64<false, LD, PUSH>(fin, fout, ad, p);
 }
 
 __global__ void __launch_bounds__(BLOCK_Z)
@@ -105,9 +105,18 @@ k_step_f64(const double* __restrict__ fin, double* __restrict__ fout, StepParams
     tile_f64<LoadNC>(fin, fout, p, t, blockIdx.x);
 }
 
+__global__ void __launch_bounds__(BLOCK_Z)
+k_step_f64_push(const double* __restrict__ fin, double* __restrict__ fout, StepParams p, Tiling t) {
+    tile_f64<LoadNC, true>(fin, fout, p, t, blockIdx.x);
+}
+
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
 inline void launch_step_f64(const double* fin, double* fout, const StepParams& p, const Tiling& t, cudaStream_t st) {
     k_step_f64<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, p, t);
+}
+inline void launch_step_f64_push(const double* fin, double* fout, const StepParams& p, const Tiling& t,
+                                 cudaStream_t st) {
+    k_step_f64_push<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, p, t);
 }
 
 }  // namespace lbm

@@ -64,10 +64,59 @@ struct SrcGlobal {
     }
 };
 
-// The collide of one site: src gives the 37 pulled populations, the results go to
-// fout[l * plane + o].
-template <class SRC>
-__device__ __forceinline__ void site_ff(const SRC& src, double* __restrict__ fout, int o, const StepParamsFF& p) {
+// The site's own populations (push form: collide first, then move).
+template <class LD>
+struct SrcOwn {
+    const double* __restrict__ fin;
+    int o, plane;
+    template <int L>
+    __device__ __forceinline__ double first() const { return LD::ld(fin + (L * plane + o)); }
+    template <int L>
+    __device__ __forceinline__ double again() const { return LD::ld_again(fin + (L * plane + o)); }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
+        va = LD::ld_again(fin + (pi.A * plane + o));
+        vb = LD::ld_again(fin + (pi.B * plane + o));
+    }
+};
+
+// Where the results go.  Pull form: every population at the site, fout[l * plane + o].
+struct DstSite {
+    double* __restrict__ fout;
+    int o, plane;
+    template <int L>
+    __device__ __forceinline__ void put(double v) const { fout[L * plane + o] = v; }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
+        fout[pi.A * plane + o] = va;
+        fout[pi.B * plane + o] = vb;
+    }
+};
+
+// Push form: each population where it moves to (interior sites through the push bases of
+// the tile, wall sites through the mirrored bounce-back rule).
+template <bool WALL>
+struct DstPush {
+    double* __restrict__ fout;
+    const SiteAddr& ad;
+    const int* pbase;     // interior push bases (fill_push_bases)
+    template <int L>
+    __device__ __forceinline__ void put(double v) const {
+        if constexpr (WALL) fout[ad.template push_dst<L, true>()] = v;
+        else fout[pbase[L] + ad.z] = v;
+    }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
+        if constexpr (WALL) {
+            fout[ad.template push_dst_rt<true>(pi.A, pi.B, pi.cx, pi.cz)] = va;
+            fout[ad.template push_dst_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)] = vb;
+        } else {
+            fout[pbase[pi.A] + ad.z] = va;
+            fout[pbase[pi.B] + ad.z] = vb;
+        }
+    }
+};
+
+// The collide of one site: src gives its 37 populations g, dst takes the 37 results.
+template <class SRC, class DST>
+__device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p) {
     // -- pass 1: moments in 64-bit fixed point ---------------------------------------------
     // pair sums by shell, pair differences grouped by |c_x| and |c_z| (no multiplies)
     int64_t R, Jx, Jz, E = 0;
@@ -135,7 +184,7 @@ __device__ __forceinline__ void site_ff(const SRC& src, double* __restrict__ fou
     {
         const double v0 = src.template again<0>();
         const ff W0 = ff_mul_c3(rho, p.wsh[0]);
-        fout[o] = fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00))));
+        dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00)))));
     }
     // Loop over the shells; each shell (2 or 4 pairs) is processed two pairs at a time, so
     // two independent dependency chains are in flight per thread.
@@ -154,8 +203,7 @@ __device__ __forceinline__ void site_ff(const SRC& src, double* __restrict__ fou
         // w f^eq of the pair in binary64, then f' = (1 - w) g + w f^eq by one FP64 FMA each
         const double Xp = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, Pb)));
         const double Xm = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, ff_neg(Pb))));
-        fout[pi.A * p.plane + o] = fma(p.one_m_omega_d, va, Xp);
-        fout[pi.B * p.plane + o] = fma(p.one_m_omega_d, vb, Xm);
+        dst.pair(pi, fma(p.one_m_omega_d, va, Xp), fma(p.one_m_omega_d, vb, Xm));
     };
 #pragma unroll 1
     for (int sh = 1; sh < NSHELL; sh++) {
@@ -190,8 +238,27 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
     SiteAddr ad;
     bool wall;
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, fout, ad.dst(), p);
-    else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, fout, ad.dst(), p);
+    const DstSite dst{fout, ad.dst(), p.plane};
+    if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, dst, p);
+    else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, dst, p);
+}
+
+// Push form of one tile: aligned reads of the site's own populations, results written
+// where they move to; pbase: Q ints of shared memory (push bases of interior tiles).
+template <class LD>
+__device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, double* __restrict__ fout,
+                                            const StepParamsFF& p, Tiling t, int b, int* pbase) {
+    const bool wall_tile = tile_is_wall(t, b);
+    if (!wall_tile) {
+        fill_push_bases(pbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+        __syncthreads();
+    }
+    SiteAddr ad;
+    bool wall;
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+    const SrcOwn<LD> src{fin, ad.dst(), p.plane};
+    if (wall) site_ff(src, DstPush<true>{fout, ad, pbase}, p);
+    else site_ff(src, DstPush<false>{fout, ad, pbase}, p);
 }
 
 // 7 resident blocks per SM (72 registers, 28 warps): measured best; 8 spills
@@ -225,6 +292,18 @@ inline StepParamsFF ff_params(const StepParams& p, const double* w_shell) {
     q.us_z = ff_host(p.us_z);
     q.T_shift = ff_host(p.T_shift);
     return q;
+}
+
+__global__ void __launch_bounds__(BLOCK_Z, 7)
+k_step_ff_push(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
+    __shared__ int pbase[Q];
+    tile_ff_push<LoadNC>(fin, fout, p, t, blockIdx.x, pbase);
+}
+
+inline void launch_step_ff_push(const double* fin, double* fout, const StepParams& p, const double* w_shell,
+                                const Tiling& t, cudaStream_t st) {
+    const StepParamsFF q = ff_params(p, w_shell);
+    k_step_ff_push<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
 }
 
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).

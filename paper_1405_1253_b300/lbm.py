@@ -41,6 +41,8 @@ _SIGS = {
     "lbm_destroy": (_i, [_vp]),
     "lbm_init_layers": (_i, [_vp, ctypes.POINTER(LayersDesc)]),
     "lbm_step": (_i, [_vp, _i]),
+    "lbm_step_push": (_i, [_vp, _i]),
+    "lbm_propagate": (_i, [_vp]),
     "lbm_current": (_vp, [_vp]),
     "lbm_get_populations": (_i, [_vp, _vp, _i]),
     "lbm_set_populations": (_i, [_vp, _vp, _i]),
@@ -173,6 +175,14 @@ class Lattice:
 
     def step(self, n: int = 1):
         _check(_lib.lbm_step(self.ctx, int(n)))
+
+    def step_push(self, n: int = 1):
+        """Push-form steps of a post-propagation state (see lbm_step_push)."""
+        _check(_lib.lbm_step_push(self.ctx, int(n)))
+
+    def propagate(self):
+        """One propagate + bc without collide (pull-form state -> push-form state)."""
+        _check(_lib.lbm_propagate(self.ctx))
 
     def sync(self):
         _check(_lib.lbm_sync(self.ctx))
