@@ -127,6 +127,16 @@ void *lbm_current(lbm_ctx *c);
 int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
 int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
 
+/* Host-buffer stepping, streamed: for t = 0..n-1 the state host_in[t] (canonical FP64
+ * f[l][x][z], 37*Lx*Lz doubles) is copied in, advanced one step (lbm_step), and the result
+ * copied out to host_out[t].  The copy out of step t-1 and the copy in of step t run
+ * concurrently on two copy streams (one per direction of the host link), each step on the
+ * context's stream once both are done with its buffers; with pinned host buffers the
+ * transfer time per step is that of one direction.  Uses the context's two buffers (the
+ * device holds the last step's output afterwards).  FP64 storage (LBM_F64, LBM_F64_FF)
+ * only; LBM_EINVAL otherwise or for NULL buffers.  Synchronises before returning.       */
+int lbm_step_host(lbm_ctx *c, const double *const *host_in, double *const *host_out, int n);
+
 /* Per-site fields of the current (post-collision) state, Sec. III.A: rho, u, T with
  * D rho T = sum |xi - u|^2 f.  renormalised = 1 returns u^H = u - gvec/2 (the paper's
  * u + dt g/2 of the pre-collision state) and T^H = T + g^2/(4 D).  Each output is an

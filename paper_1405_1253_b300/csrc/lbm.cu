@@ -158,6 +158,9 @@ struct lbm_ctx {
     double* dLrow = nullptr;    // Lz doubles (width gradient)
     double* colred = nullptr;   // 2 * Lx (init adjoint per-column sums)
     unsigned int* err = nullptr;  // device error word
+    // host-buffer stepping (lbm_step_host): copy streams and their events, made on first use
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t e_in = nullptr, e_step = nullptr, e_out = nullptr;
 };
 
 static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
@@ -194,6 +197,10 @@ static void free_ctx(lbm_ctx* c) {
     void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err};
     for (void* p : ps)
         if (p) cudaFree(p);
+    for (cudaStream_t st : {c->s_in, c->s_out})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : {c->e_in, c->e_step, c->e_out})
+        if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -467,6 +474,52 @@ int lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
     if (!c || !f) return fail(LBM_EINVAL, "NULL argument");
     DeviceGuard dg(c->device);
     return convert_pops(c, const_cast<double*>(f), on_device, false);
+}
+
+int lbm_step_host(lbm_ctx* c, const double* const* host_in, double* const* host_out, int n) {
+    if (!c || !host_in || !host_out) return fail(LBM_EINVAL, "NULL argument");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    if (pop_bytes(c->prec) != 8) return fail(LBM_EINVAL, "lbm_step_host needs FP64 storage");
+    for (int t = 0; t < n; t++)
+        if (!host_in[t] || !host_out[t]) return fail(LBM_EINVAL, "host buffer %d is NULL", t);
+    DeviceGuard dg(c->device);
+    if (!c->s_in) {
+        bool ok = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->e_in, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->e_step, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->e_out, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return fail(LBM_ECUDA, "copy streams could not be created");
+    }
+    const size_t bytes = (size_t)Q * c->Lx * c->Lz * sizeof(double);
+    const StepParams p = step_params(c);
+    const Tiling tl = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    void* X = c->buf[c->cur];         // the step's input, filled from the host
+    void* Y = c->buf[c->cur ^ 1];     // the step's output, read back to the host
+    // Step t: X <- host_in[t] (s_in), Y = step(X) (c's stream), host_out[t] <- Y (s_out).
+    // The copy in of step t waits until step t-1 has read X; the step waits for its copy
+    // in and for the copy out of step t-1 to have read Y.  So the copy out of step t-1
+    // and the copy in of step t run at the same time, one per direction of the link.
+    CU(cudaEventRecord(c->e_step, c->stream));
+    CU(cudaEventRecord(c->e_out, c->stream));
+    for (int t = 0; t < n; t++) {
+        CU(cudaStreamWaitEvent(c->s_in, c->e_step, 0));
+        CU(cudaMemcpyAsync(X, host_in[t], bytes, cudaMemcpyHostToDevice, c->s_in));
+        CU(cudaEventRecord(c->e_in, c->s_in));
+        CU(cudaStreamWaitEvent(c->stream, c->e_in, 0));
+        CU(cudaStreamWaitEvent(c->stream, c->e_out, 0));
+        launch_step(c->prec, X, Y, p, tl, c->stream);
+        LAUNCH_CHECK();
+        CU(cudaEventRecord(c->e_step, c->stream));
+        CU(cudaStreamWaitEvent(c->s_out, c->e_step, 0));
+        CU(cudaMemcpyAsync(host_out[t], Y, bytes, cudaMemcpyDeviceToHost, c->s_out));
+        CU(cudaEventRecord(c->e_out, c->s_out));
+    }
+    CU(cudaStreamSynchronize(c->s_in));
+    CU(cudaStreamSynchronize(c->s_out));
+    CU(cudaStreamSynchronize(c->stream));
+    if (n > 0) c->cur ^= 1;           // the device now holds the last step's output
+    return LBM_OK;
 }
 
 // ---------------------------------------------------------------------------------

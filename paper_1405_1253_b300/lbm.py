@@ -42,6 +42,7 @@ _SIGS = {
     "lbm_init_layers": (_i, [_vp, ctypes.POINTER(LayersDesc)]),
     "lbm_step": (_i, [_vp, _i]),
     "lbm_step_push": (_i, [_vp, _i]),
+    "lbm_step_host": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i]),
     "lbm_propagate": (_i, [_vp]),
     "lbm_current": (_vp, [_vp]),
     "lbm_get_populations": (_i, [_vp, _vp, _i]),
@@ -175,6 +176,19 @@ class Lattice:
 
     def step(self, n: int = 1):
         _check(_lib.lbm_step(self.ctx, int(n)))
+
+    def step_host(self, host_in, host_out):
+        """One step per (input, output) pair of host buffers (pinned torch tensors or
+        contiguous float64 numpy arrays of 37*Lx*Lz elements): copy in, step, copy out,
+        the copies of consecutive steps overlapped (lbm_step_host)."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        n = len(host_in)
+        if len(host_out) != n:
+            raise ValueError("host_in and host_out differ in length")
+        ins = (_vp * n)(*[ptr(a) for a in host_in])
+        outs = (_vp * n)(*[ptr(a) for a in host_out])
+        _check(_lib.lbm_step_host(self.ctx, ins, outs, n))
 
     def step_push(self, n: int = 1):
         """Push-form steps of a post-propagation state (see lbm_step_push)."""
