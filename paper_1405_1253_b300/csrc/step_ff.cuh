@@ -114,10 +114,14 @@ struct DstPush {
     }
 };
 
-// The collide of one site: src gives its 37 populations g, dst takes the 37 results.
-template <class SRC, class DST>
-__device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p) {
-    // -- pass 1: moments in 64-bit fixed point ---------------------------------------------
+// Moments of one site in 64-bit fixed point (unit 2^-60): rho, J = sum c g, E = sum |c|^2 g.
+struct MomentsFix {
+    int64_t R, Jx, Jz, E;
+};
+
+// Pass 1: the moments of the site's 37 populations g (src.first<L>()).
+template <class SRC>
+__device__ __forceinline__ MomentsFix moments_ff(const SRC& src) {
     // pair sums by shell, pair differences grouped by |c_x| and |c_z| (no multiplies)
     int64_t R, Jx, Jz, E = 0;
     int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -148,6 +152,14 @@ __device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const St
     });
     Jx = GX[1] + 2 * GX[2] + 3 * GX[3];
     Jz = GZ[1] + 2 * GZ[2] + 3 * GZ[3];
+    return MomentsFix{R, Jx, Jz, E};
+}
+
+// The rest of the collide of one site from its moments m: per-site scalars, equilibrium,
+// relaxation; src.again / src.pair give the populations g again, dst takes the results.
+template <class SRC, class DST>
+__device__ __forceinline__ void collide_ff(const MomentsFix& m, const SRC& src, const DST& dst, const StepParamsFF& p) {
+    const int64_t R = m.R, Jx = m.Jx, Jz = m.Jz, E = m.E;
     // -- per-site scalars in float-float (the 2^60 scale cancels in the ratios) -----------
     const double Rd = __ll2double_rn(R);
     const ff rho = dsplit(Rd), jx = i64_to_ff(Jx), jz = i64_to_ff(Jz);
@@ -223,6 +235,12 @@ __device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const St
             pair_out(p1, K0, K1, K2, W, v1a, v1b);
         }
     }
+}
+
+// The collide of one site: src gives its 37 populations g, dst takes the 37 results.
+template <class SRC, class DST>
+__device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p) {
+    collide_ff(moments_ff(src), src, dst, p);
 }
 
 // One tile b of the lattice tiling t, pulled from global memory; sbase: Q ints of shared
