@@ -12,8 +12,8 @@ __constant__ DevLattice d_lat;
 // The 18 opposite velocity pairs for loops that run over pairs at run time
 // (filled from the compile-time tables of lattice.cuh at upload).
 struct PairInfo {
-    int A, B, cx, cz, c2, shell;
-    float fcx, fcz, fc2;        // the same integers as FP32 (no conversion in the loop)
+    int A, B, cx, cz;
+    float fcx, fcz, fc2;        // c_x, c_z and |c|^2 as FP32 (no conversion in the loop)
 };
 __constant__ PairInfo d_pairs[18];
 // Pairs are grouped by shell in canonical order: shell s owns pairs

@@ -67,7 +67,7 @@ struct DevLattice {
     double w[NSHELL];      // shell weights
     double r, r2;          // lattice constant and its square
     double r2_half;        // r^2 / 2
-    float r_hi, r_lo, r2_hi, r2_lo;
+    float r_hi, r2_hi;     // FP32 r and r^2 (FP32 collide)
     float wf[NSHELL];      // FP32 weights
     // constants of the float-float collide as three FP32 terms each (no representation
     // error that would bias every step): r, and 6 r^2, 12 r^2, 3 r^4 of the coefficients of 24 P(s)

@@ -86,11 +86,6 @@ static int host_quadrature(Quadrature* out) {
     return LBM_OK;
 }
 
-static void split_ff(double v, float& hi, float& lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
 static void split3(long double v, float (&t)[3]) {
     t[0] = (float)v;
     t[1] = (float)(v - (long double)t[0]);
@@ -112,8 +107,8 @@ static int upload_lattice(int dev) {
     h.r = q.r;
     h.r2 = q.r * q.r;
     h.r2_half = 0.5 * h.r2;
-    split_ff(h.r, h.r_hi, h.r_lo);
-    split_ff(h.r2, h.r2_hi, h.r2_lo);
+    h.r_hi = (float)h.r;
+    h.r2_hi = (float)h.r2;
     const long double rl = q.r, r2l = rl * rl;
     split3(rl, h.r3);
     split3(6.0L * r2l, h.r2x6);
@@ -123,7 +118,7 @@ static int upload_lattice(int dev) {
     PairInfo pairs[NPAIR];
     for (int k = 0; k < NPAIR; k++) {
         const int A = pair_first(k);
-        pairs[k] = PairInfo{A, opp(A), cx(A), cz(A), c2(A), shell_of(A), (float)cx(A), (float)cz(A), (float)c2(A)};
+        pairs[k] = PairInfo{A, opp(A), cx(A), cz(A), (float)cx(A), (float)cz(A), (float)c2(A)};
     }
     CU(cudaMemcpyToSymbol(d_pairs, pairs, sizeof pairs));
     int sfirst[NSHELL] = {0}, snp[NSHELL] = {0}, vel[Q][2];
