@@ -293,6 +293,12 @@ int lbm_slabs_step(lbm_slabs *s, int nsteps, int overlap);
 /* Copy the slabs' state back into the context's current buffer; synchronises.       */
 int lbm_slabs_gather(lbm_slabs *s);
 
+/* Test hook for the error paths: the n-th next device allocation made by the library
+ * (n = 0: the next one) is refused as if the device were out of memory; the caller
+ * reports LBM_ENOMEM.  One refusal per call of this function; n < 0 cancels a pending one.
+ * The paper has no counterpart.                                                       */
+int lbm_test_fail_alloc(int n);
+
 /* Message of the last failed call on this thread ("" if none).                        */
 const char *lbm_last_error(void);
 

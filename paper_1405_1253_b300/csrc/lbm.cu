@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -62,6 +63,38 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
     }
 };
+
+// ---------------------------------------------------------------------------------
+// Device allocations of the library go through dev_malloc / dev_malloc_async, so that a test
+// can refuse the n-th next one (lbm_test_fail_alloc) and check that every caller reports
+// LBM_ENOMEM and leaves nothing half-built.
+// ---------------------------------------------------------------------------------
+static std::atomic<int> g_fail_alloc{-1};
+
+static bool alloc_refused() {
+    int n = g_fail_alloc.load();
+    while (n >= 0)
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 0;
+    return false;
+}
+
+template <class T>
+static cudaError_t dev_malloc(T** p, size_t bytes) {
+    if (alloc_refused()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc((void**)p, bytes);
+}
+
+template <class T>
+static cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+    if (alloc_refused()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync((void**)p, bytes, st);
+}
 
 // ---------------------------------------------------------------------------------
 // Lattice constants: solved once on the host, uploaded once per device.
@@ -181,7 +214,7 @@ static int ensure_part(lbm_ctx* c, size_t n) {
     }
     c->part = nullptr;
     c->part_cap = 0;
-    if (cudaMalloc(&c->part, n * sizeof(double)) != cudaSuccess)
+    if (dev_malloc(&c->part, n * sizeof(double)) != cudaSuccess)
         return fail(LBM_ENOMEM, "cannot allocate %zu reduction doubles", n);
     c->part_cap = n;
     return LBM_OK;
@@ -219,6 +252,11 @@ static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, doub
 extern "C" {
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_test_fail_alloc(int n) {
+    g_fail_alloc.store(n < 0 ? -1 : n);
+    return LBM_OK;
+}
 
 int lbm_lattice(int* c, double* w, double* r) {
     Quadrature q;
@@ -260,11 +298,11 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     c->buf[0] = buf0; c->buf[1] = buf1; c->bytes = bytes; c->cur = 0;
     c->stream = (cudaStream_t)cuda_stream;
     c->device = a0.device;
-    bool ok = cudaMalloc(&c->zcol, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c->small, ((size_t)Lz + 8) * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c->dLrow, (size_t)Lz * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c->colred, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&c->err, sizeof(unsigned int)) == cudaSuccess;
+    bool ok = dev_malloc(&c->zcol, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
+              dev_malloc(&c->small, ((size_t)Lz + 8) * sizeof(double)) == cudaSuccess &&
+              dev_malloc(&c->dLrow, (size_t)Lz * sizeof(double)) == cudaSuccess &&
+              dev_malloc(&c->colred, 2 * (size_t)Lx * sizeof(double)) == cudaSuccess &&
+              dev_malloc(&c->err, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
         return fail(LBM_ENOMEM, "context scratch allocation failed");
@@ -323,7 +361,7 @@ static int fill_init_params(lbm_ctx* c, const lbm_layers_desc* d, InitParams* ip
         }
         c->modes = nullptr;
         c->modes_cap = 0;
-        if (cudaMalloc(&c->modes, 4 * (size_t)cap * sizeof(double)) != cudaSuccess)
+        if (dev_malloc(&c->modes, 4 * (size_t)cap * sizeof(double)) != cudaSuccess)
             return fail(LBM_ENOMEM, "mode buffer allocation failed");
         c->modes_cap = cap;
     }
@@ -435,7 +473,7 @@ static int convert_pops(lbm_ctx* c, double* buf, int on_device, bool to_f64) {
     // FP32 storage: convert one population plane at a time through device scratch
     const long long chunk = (long long)c->Lx * c->Lz;
     double* tmp = nullptr;
-    if (!on_device && cudaMallocAsync((void**)&tmp, chunk * sizeof(double), c->stream) != cudaSuccess)
+    if (!on_device && dev_malloc_async(&tmp, chunk * sizeof(double), c->stream) != cudaSuccess)
         return fail(LBM_ENOMEM, "conversion buffer allocation failed");
     for (long long first = 0; first < n; first += chunk) {
         const long long m = std::min(chunk, n - first);
@@ -531,7 +569,7 @@ int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int 
         int k = 0;
         for (int i = 0; i < 4; i++) k += outs[i] != nullptr;
         if (k == 0) return LBM_OK;
-        if (cudaMallocAsync((void**)&tmp, k * n * sizeof(double), c->stream) != cudaSuccess)
+        if (dev_malloc_async(&tmp, k * n * sizeof(double), c->stream) != cudaSuccess)
             return fail(LBM_ENOMEM, "moments buffer allocation failed");
         k = 0;
         for (int i = 0; i < 4; i++) dev[i] = outs[i] ? tmp + (k++) * n : nullptr;
@@ -855,9 +893,9 @@ int lbm_ensemble_create(lbm_ensemble** out, int n, lbm_ctx* const* ctxs) {
     e->device = ctxs[0]->device;
     e->stream = ctxs[0]->stream;
     e->ctx.assign(ctxs, ctxs + n);
-    bool ok = cudaMalloc(&e->d_lats, n * sizeof(EnsLattice)) == cudaSuccess &&
-              cudaMalloc(&e->d_ctl, sizeof(EnsControl)) == cudaSuccess &&
-              cudaMalloc(&e->d_done, n * sizeof(unsigned int)) == cudaSuccess;
+    bool ok = dev_malloc(&e->d_lats, n * sizeof(EnsLattice)) == cudaSuccess &&
+              dev_malloc(&e->d_ctl, sizeof(EnsControl)) == cudaSuccess &&
+              dev_malloc(&e->d_done, n * sizeof(unsigned int)) == cudaSuccess;
     if (!ok) {
         cudaFree(e->d_lats); cudaFree(e->d_ctl); cudaFree(e->d_done);
         delete e;
@@ -1170,7 +1208,7 @@ int lbm_slabs_create(lbm_slabs** out, lbm_ctx* c, int nslab) {
     s->slab_elems = (size_t)Q * s->W * c->Lz;
     bool ok = (long long)s->slab_elems < (1LL << 31);
     for (int i = 0; ok && i < 2; i++)
-        ok = cudaMalloc(&s->buf[i], (size_t)nslab * s->slab_elems * s->es) == cudaSuccess &&
+        ok = dev_malloc(&s->buf[i], (size_t)nslab * s->slab_elems * s->es) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->ev_bulk[i], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->ev_comm[i], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&s->bulk, cudaStreamNonBlocking) == cudaSuccess;

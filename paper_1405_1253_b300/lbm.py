@@ -73,12 +73,19 @@ _SIGS = {
     "lbm_slabs_scatter": (_i, [_vp]),
     "lbm_slabs_step": (_i, [_vp, _i, _i]),
     "lbm_slabs_gather": (_i, [_vp]),
+    "lbm_test_fail_alloc": (_i, [_i]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.restype = _res
     _fn.argtypes = _args
+
+
+def test_fail_alloc(n: int):
+    """Refuse the n-th next device allocation of the library (n < 0: cancel); for tests of
+    the error paths."""
+    _lib.lbm_test_fail_alloc(int(n))
 
 
 class LBMError(RuntimeError):
