@@ -293,6 +293,12 @@ int lbm_slabs_step(lbm_slabs *s, int nsteps, int overlap);
 /* Copy the slabs' state back into the context's current buffer; synchronises.       */
 int lbm_slabs_gather(lbm_slabs *s);
 
+/* Bounds-checked builds (liblbm_checked.so, compiled with -DLBM_BOUNDS_CHECK): *out = the
+ * number of out-of-range population indices the kernels met on the current device since the
+ * last call (each one was redirected to element 0 instead of being used); the count is reset.
+ * Synchronises the device.  Other builds: LBM_ESTATE.  The paper has no counterpart.     */
+int lbm_test_oob_count(unsigned int *out);
+
 /* Test hook for the error paths: the n-th next device allocation made by the library
  * (n = 0: the next one) is refused as if the device were out of memory; the caller
  * reports LBM_ENOMEM.  One refusal per call of this function; n < 0 cancels a pending one.

@@ -8,6 +8,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "liblbm.so")
+# the same library with every population load and store index-checked (LBM_BOUNDS_CHECK):
+# an out-of-range index is counted and redirected to element 0 instead of being used
+LIB_CHECKED = os.path.join(CSRC, "liblbm_checked.so")
 SOURCES = [os.path.join(CSRC, "lbm.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -23,12 +26,15 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile liblbm.so if it is missing or older than its sources."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile liblbm.so (or, checked=True, liblbm_checked.so) if it is missing or older
+    than its sources."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-           "-Xcompiler", "-fPIC", "-shared", "-o", LIB + ".tmp", *SOURCES, "-lcudart"]
+           *(["-DLBM_BOUNDS_CHECK"] if checked else []),
+           "-Xcompiler", "-fPIC", "-shared", "-o", lib + ".tmp", *SOURCES, "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -36,10 +42,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
     if verbose:
         sys.stderr.write(res.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force=True, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force=True, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -55,7 +55,8 @@ k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next
 #pragma unroll
     for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
     double g[Q];
-    static_for<Q>([&](auto l) { g[l.value] = ft[pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane)]; });
+    const int n = Q * p.plane;
+    static_for<Q>([&](auto l) { g[l.value] = ft[LBM_IDX(pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane), n)]; });
     const double r = d_lat.r, r2 = d_lat.r2;
     double R = g[0], Jx = 0.0, Jz = 0.0, E = 0.0;
     static_for<NPAIR>([&](auto k) {
@@ -74,7 +75,7 @@ k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next
     const double u2 = usx * usx + usz * usz;
     const double a = r * usx, b = r * usz;          // s_l = c_x a + c_z b
     const int o = x * p.Lz + z;
-    const double lam0 = lam_next[o];
+    const double lam0 = lam_next[LBM_IDX(o, n)];
     // rest population (s = 0, C2 = 0)
     double A = d_lat.w[0] * lam0 * (1.0 - 0.5 * u2 - th + 0.125 * u2 * u2 + th * u2 + th * th);
     double Bx = 0.0, Bz = 0.0, Bu = d_lat.w[0] * lam0 * (-0.5 + 0.25 * u2 + th);
@@ -98,7 +99,7 @@ k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next
         const double O1 = s * fma(q, 1.0 / 6.0, 2.0 * K2);
         const double G0 = -0.5 + 0.25 * u2 - 0.25 * th * (C2 - 4.0);
         const double H0 = 0.5 * (C2 - 2.0) - 0.25 * u2 * (C2 - 4.0) + 0.25 * th * (C2 * C2 - 8.0 * C2 + 8.0);
-        const double la = lam_next[A_ * p.plane + o], lb = lam_next[B_ * p.plane + o];
+        const double la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
         const double w = d_lat.w[SH];
         const double ls = w * (la + lb), ld = w * (la - lb);
         A = fma(ls, Ev, fma(ld, Od, A));
@@ -118,14 +119,14 @@ k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next
     const double Bpz = Bzt * inv - 2.0 * Ct * uz / Dr;
     const double Cp = Ct / Dr;
     // scatter mu to the pull sources (unique targets: propagate + bc is a permutation)
-    lam_out[pull_index<0>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, lam0, p.omega * Ap);
+    lam_out[LBM_IDX(pull_index<0>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, lam0, p.omega * Ap);
     static_for<NPAIR>([&](auto k) {
         constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
         const double ev = fma(Cp, r2 * c2(A_), Ap);
         const double od = fma(Bpx, r * cx(A_), Bpz * (r * cz(A_)));
-        const double la = lam_next[A_ * p.plane + o], lb = lam_next[B_ * p.plane + o];
-        lam_out[pull_index<A_>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, la, p.omega * (ev + od));
-        lam_out[pull_index<B_>(x, z, col, p.Lz, p.plane)] = fma(p.one_m_omega, lb, p.omega * (ev - od));
+        const double la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
+        lam_out[LBM_IDX(pull_index<A_>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, la, p.omega * (ev + od));
+        lam_out[LBM_IDX(pull_index<B_>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, lb, p.omega * (ev - od));
     });
 }
 

@@ -22,6 +22,21 @@ __constant__ int d_shell_first[8];
 __constant__ int d_shell_npair[8];
 __constant__ int d_vel[37][2];
 
+// Bounds-checked builds (-DLBM_BOUNDS_CHECK): LBM_IDX(i, n) tests every population index
+// against the element count n of its buffer; an index outside [0, n) is counted in
+// g_oob_count and replaced by 0, so the access stays in the buffer.  Other builds use i.
+#ifdef LBM_BOUNDS_CHECK
+__device__ unsigned int g_oob_count;
+__device__ __forceinline__ int checked_index(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
+    atomicAdd(&g_oob_count, 1u);
+    return 0;
+}
+#define LBM_IDX(i, n) checked_index((i), (n))
+#else
+#define LBM_IDX(i, n) (i)
+#endif
+
 constexpr int DIM = 2;
 constexpr int BLOCK_Z = 128;      // threads per block along z (one site per thread)
 
@@ -229,20 +244,24 @@ template <bool PUSH, bool WALL, class LD, class T>
 __device__ __forceinline__ void load_site(const T* __restrict__ fin, const SiteAddr& ad, T (&g)[Q]) {
     if constexpr (PUSH) {
         const int o = ad.dst();
-        static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + (l.value * ad.plane + o)); });
+        static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + LBM_IDX(l.value * ad.plane + o, Q * ad.plane)); });
     } else {
-        static_for<Q>([&](auto l) { g[l.value] = LD::ld(fin + ad.template src<decltype(l)::value, WALL>()); });
+        static_for<Q>([&](auto l) {
+            g[l.value] = LD::ld(fin + LBM_IDX((ad.template src<decltype(l)::value, WALL>()), Q * ad.plane));
+        });
     }
 }
 // ... and the 37 results, stored at the site (PUSH = false) or where they move to.
 template <bool PUSH, bool WALL, class T>
 __device__ __forceinline__ void store_site(T* __restrict__ fout, const SiteAddr& ad, const T (&fo)[Q]) {
     if constexpr (PUSH) {
-        static_for<Q>([&](auto l) { fout[ad.template push_dst<decltype(l)::value, WALL>()] = fo[l.value]; });
+        static_for<Q>([&](auto l) {
+            fout[LBM_IDX((ad.template push_dst<decltype(l)::value, WALL>()), Q * ad.plane)] = fo[l.value];
+        });
     } else {
         const int o = ad.dst();
 #pragma unroll
-        for (int l = 0; l < Q; l++) fout[l * ad.plane + o] = fo[l];
+        for (int l = 0; l < Q; l++) fout[LBM_IDX(l * ad.plane + o, Q * ad.plane)] = fo[l];
     }
 }
 

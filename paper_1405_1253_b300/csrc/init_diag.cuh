@@ -365,8 +365,13 @@ k_propagate(const T* __restrict__ fin, T* __restrict__ fout, int Lx, int Lz, Til
     bool wall;
     if (!ad.setup(Lx, Lz, Lx * Lz, t, blockIdx.x, wall)) return;
     const int o = ad.dst();
-    if (wall) static_for<Q>([&](auto l) { fout[l.value * ad.plane + o] = fin[ad.template src<decltype(l)::value, true>()]; });
-    else static_for<Q>([&](auto l) { fout[l.value * ad.plane + o] = fin[ad.template src<decltype(l)::value, false>()]; });
+    const int n = Q * ad.plane;
+    if (wall) static_for<Q>([&](auto l) {
+        fout[LBM_IDX(l.value * ad.plane + o, n)] = fin[LBM_IDX((ad.template src<decltype(l)::value, true>()), n)];
+    });
+    else static_for<Q>([&](auto l) {
+        fout[LBM_IDX(l.value * ad.plane + o, n)] = fin[LBM_IDX((ad.template src<decltype(l)::value, false>()), n)];
+    });
 }
 
 // ---------------------------------------------------------------------------------

@@ -253,6 +253,20 @@ extern "C" {
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
 
+int lbm_test_oob_count(unsigned int* out) {
+#ifdef LBM_BOUNDS_CHECK
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpyFromSymbol(out, g_oob_count, sizeof(unsigned int)));
+    const unsigned int zero = 0;
+    CU(cudaMemcpyToSymbol(g_oob_count, &zero, sizeof zero));
+    return LBM_OK;
+#else
+    (void)out;
+    return fail(LBM_ESTATE, "not a bounds-checked build");
+#endif
+}
+
 int lbm_test_fail_alloc(int n) {
     g_fail_alloc.store(n < 0 ? -1 : n);
     return LBM_OK;

@@ -46,8 +46,8 @@ struct SrcGlobal {
     const int* sbase;     // interior pull bases (fill_pull_bases)
     template <int L>
     __device__ __forceinline__ int idx() const {
-        if constexpr (WALL) return ad.template src<L, true>();
-        else return sbase[L] + ad.z;
+        if constexpr (WALL) return LBM_IDX((ad.template src<L, true>()), Q * ad.plane);
+        else return LBM_IDX(sbase[L] + ad.z, Q * ad.plane);
     }
     template <int L>
     __device__ __forceinline__ double first() const { return LD::ld(fin + idx<L>()); }
@@ -55,11 +55,11 @@ struct SrcGlobal {
     __device__ __forceinline__ double again() const { return LD::ld_again(fin + idx<L>()); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
         if constexpr (WALL) {
-            va = LD::ld_again(fin + ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz));
-            vb = LD::ld_again(fin + ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz));
+            va = LD::ld_again(fin + LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane));
+            vb = LD::ld_again(fin + LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane));
         } else {
-            va = LD::ld_again(fin + (sbase[pi.A] + ad.z));   // one 32-bit add, one address add
-            vb = LD::ld_again(fin + (sbase[pi.B] + ad.z));
+            va = LD::ld_again(fin + LBM_IDX(sbase[pi.A] + ad.z, Q * ad.plane));   // one 32-bit add, one address add
+            vb = LD::ld_again(fin + LBM_IDX(sbase[pi.B] + ad.z, Q * ad.plane));
         }
     }
 };
@@ -70,12 +70,12 @@ struct SrcOwn {
     const double* __restrict__ fin;
     int o, plane;
     template <int L>
-    __device__ __forceinline__ double first() const { return LD::ld(fin + (L * plane + o)); }
+    __device__ __forceinline__ double first() const { return LD::ld(fin + LBM_IDX(L * plane + o, Q * plane)); }
     template <int L>
-    __device__ __forceinline__ double again() const { return LD::ld_again(fin + (L * plane + o)); }
+    __device__ __forceinline__ double again() const { return LD::ld_again(fin + LBM_IDX(L * plane + o, Q * plane)); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
-        va = LD::ld_again(fin + (pi.A * plane + o));
-        vb = LD::ld_again(fin + (pi.B * plane + o));
+        va = LD::ld_again(fin + LBM_IDX(pi.A * plane + o, Q * plane));
+        vb = LD::ld_again(fin + LBM_IDX(pi.B * plane + o, Q * plane));
     }
 };
 
@@ -84,10 +84,10 @@ struct DstSite {
     double* __restrict__ fout;
     int o, plane;
     template <int L>
-    __device__ __forceinline__ void put(double v) const { fout[L * plane + o] = v; }
+    __device__ __forceinline__ void put(double v) const { fout[LBM_IDX(L * plane + o, Q * plane)] = v; }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
-        fout[pi.A * plane + o] = va;
-        fout[pi.B * plane + o] = vb;
+        fout[LBM_IDX(pi.A * plane + o, Q * plane)] = va;
+        fout[LBM_IDX(pi.B * plane + o, Q * plane)] = vb;
     }
 };
 
@@ -100,16 +100,16 @@ struct DstPush {
     const int* pbase;     // interior push bases (fill_push_bases)
     template <int L>
     __device__ __forceinline__ void put(double v) const {
-        if constexpr (WALL) fout[ad.template push_dst<L, true>()] = v;
-        else fout[pbase[L] + ad.z] = v;
+        if constexpr (WALL) fout[LBM_IDX((ad.template push_dst<L, true>()), Q * ad.plane)] = v;
+        else fout[LBM_IDX(pbase[L] + ad.z, Q * ad.plane)] = v;
     }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
         if constexpr (WALL) {
-            fout[ad.template push_dst_rt<true>(pi.A, pi.B, pi.cx, pi.cz)] = va;
-            fout[ad.template push_dst_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)] = vb;
+            fout[LBM_IDX((ad.template push_dst_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane)] = va;
+            fout[LBM_IDX((ad.template push_dst_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane)] = vb;
         } else {
-            fout[pbase[pi.A] + ad.z] = va;
-            fout[pbase[pi.B] + ad.z] = vb;
+            fout[LBM_IDX(pbase[pi.A] + ad.z, Q * ad.plane)] = va;
+            fout[LBM_IDX(pbase[pi.B] + ad.z, Q * ad.plane)] = vb;
         }
     }
 };

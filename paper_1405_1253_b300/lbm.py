@@ -13,7 +13,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "csrc", "liblbm.so")
+# LBM_LIBRARY selects another build of the same library (the bounds-checked one in tests)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "csrc", "liblbm.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1405_1253_b300.build` "
@@ -74,6 +75,7 @@ _SIGS = {
     "lbm_slabs_step": (_i, [_vp, _i, _i]),
     "lbm_slabs_gather": (_i, [_vp]),
     "lbm_test_fail_alloc": (_i, [_i]),
+    "lbm_test_oob_count": (_i, [ctypes.POINTER(ctypes.c_uint)]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -86,6 +88,14 @@ def test_fail_alloc(n: int):
     """Refuse the n-th next device allocation of the library (n < 0: cancel); for tests of
     the error paths."""
     _lib.lbm_test_fail_alloc(int(n))
+
+
+def test_oob_count() -> int:
+    """Out-of-range population indices met since the last call (bounds-checked builds
+    only; raises LBMError otherwise)."""
+    v = ctypes.c_uint()
+    _check(_lib.lbm_test_oob_count(ctypes.byref(v)))
+    return v.value
 
 
 class LBMError(RuntimeError):
