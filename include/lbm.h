@@ -52,9 +52,11 @@ enum {
 
 /* Population storage and collide arithmetic.
  *   LBM_F64     IEEE binary64 storage, collide in native FP64 arithmetic.
- *   LBM_F64_FF  IEEE binary64 storage, collide in float-float arithmetic (pairs of
- *               FP32 carrying a ~48-bit significand) on the FP32 and integer pipes;
- *               same storage and bytes as LBM_F64, results equal to ~1e-14 per step.
+ *   LBM_F64_FF  IEEE binary64 storage; moments summed in 64-bit integers, the rest of
+ *               the collide in float-float arithmetic (pairs of FP32 carrying a ~48-bit
+ *               significand) on the FP32 and integer pipes, one FP64 FMA per population
+ *               for the relaxation; same storage and bytes as LBM_F64, results equal to
+ *               it to ~1e-14 per step.
  *   LBM_F32     FP32 storage, FP32 collide arithmetic (compensated moment sums; the
  *               collide update is repaired to conserve mass, momentum + rho g and
  *               internal energy).                                                     */
