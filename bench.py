@@ -325,6 +325,28 @@ def bench_push(torch, lbm, lat, steps, stream):
     return out
 
 
+def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
+    """The adjoint step kernel alone on the 1024x2048 state (FP64): it reads f_t and lam_{t+1}
+    and writes lam_t, 3 x 296 = 888 algorithmic bytes per site."""
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64", stream=stream)
+    L.init_from(lat)
+    f = L.populations_device().clone()
+    lam = [torch.rand_like(f), torch.empty_like(f)]
+    L.adjoint_step(f, lam[0], lam[1])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    L.close()
+    gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
+    return {"workload": f"{lat.Lx}x{lat.Lz}, FP64, {steps} adjoint steps", "ms": ms,
+            "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak, "bytes_per_site": 888}
+
+
 def fp32_error(torch, lbm, lat, steps, stream):
     """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
     step after `steps` steps from the same initial state."""
@@ -410,6 +432,8 @@ def run_ours(args):
         extras["ensemble_f64"] = bench_ensemble(torch, lbm, "f64_ff", 100, es)
         extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", 100, es)
         extras["adjoint"] = bench_adjoint(torch)
+        extras["adjoint_kernel"] = bench_adjoint_kernel(torch, lbm, lat, 20, stream,
+                                                        float(measured_peaks()[0].get("hbm_gbs", 6400.0)))
         extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
         extras["push_vs_pull"] = bench_push(torch, lbm, lat, 200, stream)
 
