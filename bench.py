@@ -265,7 +265,7 @@ def bench_adjoint(torch):
     g_lo, g_hi = drv.backward()
     st = drv.stats
     drv.close()
-    return {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (FP64)",
+    return {"workload": f"256x512, 2000 steps, checkpoint every 100, 16 modes per front ({drv.prec})",
             "forward_s": st.forward_s, "backward_s": st.backward_s, "backward_over_forward": st.backward_s / st.forward_s,
             "memory_bytes": st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes,
             "forward_memory_bytes": 2 * st.state_bytes,
@@ -326,25 +326,28 @@ def bench_push(torch, lbm, lat, steps, stream):
 
 
 def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
-    """The adjoint step kernel alone on the 1024x2048 state (FP64): it reads f_t and lam_{t+1}
-    and writes lam_t, 3 x 296 = 888 algorithmic bytes per site."""
-    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64", stream=stream)
-    L.init_from(lat)
-    f = L.populations_device().clone()
-    lam = [torch.rand_like(f), torch.empty_like(f)]
-    L.adjoint_step(f, lam[0], lam[1])
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(steps):
-        L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    L.close()
-    gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
-    return {"workload": f"{lat.Lx}x{lat.Lz}, FP64, {steps} adjoint steps", "ms": ms,
-            "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak, "bytes_per_site": 888}
+    """The adjoint step kernel alone on the 1024x2048 state, float-float and native FP64:
+    it reads f_t and lam_{t+1} and writes lam_t, 3 x 296 = 888 algorithmic bytes per site."""
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, FP64 storage, {steps} adjoint steps", "bytes_per_site": 888}
+    for prec in ("f64_ff", "f64"):
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        f = L.populations_device().clone()
+        lam = [torch.rand_like(f), torch.empty_like(f)]
+        for i in range(3):
+            L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        L.close()
+        gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
+        out[prec] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+    return out
 
 
 def fp32_error(torch, lbm, lat, steps, stream):

@@ -180,20 +180,26 @@ int lbm_row_stats(lbm_ctx *c, double *T_mean, double *T_rms, double *Ek_mean, do
  * finite.                                                                             */
 int lbm_global_sums(lbm_ctx *c, double out[2]);
 
-/* Adjoint of one step (LBM_F64 contexts only).  With f_{t+1} = C(P f_t), P the
- * propagate+bc permutation and C the pointwise collide:
+/* Adjoint of one step (FP64 storage: LBM_F64 or LBM_F64_FF; LBM_ESTATE for LBM_F32).
+ * With f_{t+1} = C(P f_t), P the propagate+bc permutation and C the pointwise collide
+ * (Eq. (LBE) with the shifted equilibrium of Sec. III.A):
  *   lam_out = P^T J_C(P f_t)^T lam_next.
  * f_t, lam_next, lam_out: device arrays of 37*Lx*Lz doubles in the storage layout;
- * lam_out must not alias the other two.  Asynchronous.                                */
+ * lam_out must not alias the other two.  LBM_F64 evaluates the Jacobian product in
+ * native FP64; LBM_F64_FF in float-float on the FP32 pipes with one FP64 FMA per
+ * population, scaled per site by the largest exponent among its 37 lam_next values
+ * (entries more than 2^74 below that maximum count as 0 in the collide term; results
+ * agree with the native form to ~1e-15 of the site's largest |lam_next|).  Both assume
+ * |u| well below 0.3 and finite inputs.  Asynchronous.                                */
 int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, double *lam_out);
 
-/* Adjoint of the width readout (LBM_F64): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
+/* Adjoint of the width readout (FP64 storage): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
  * with dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device, FP64 layout).
  * dL_dTbar is a host array of Lz doubles.  lam_out: device, 37*Lx*Lz doubles.
  * Synchronises.                                                                       */
 int lbm_loss_adjoint(lbm_ctx *c, const double *f, const double *dL_dTbar, double *lam_out);
 
-/* Adjoint of lbm_init_layers with respect to the mode amplitudes (LBM_F64): given
+/* Adjoint of lbm_init_layers with respect to the mode amplitudes (FP64 storage): given
  * lam0 = dL/df_0 (device, FP64 layout) returns dL/damp_lo[k] and dL/damp_hi[k] in the
  * host arrays dA_lo, dA_hi (n_modes each).  Synchronises.                             */
 int lbm_init_adjoint(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,

@@ -37,9 +37,10 @@ class AdjointStats:
 
 
 class WidthGradient:
-    """Forward/backward driver for one lattice description (FP64 context)."""
+    """Forward/backward driver for one lattice description on an FP64-storage context:
+    prec "f64_ff" (float-float step and adjoint, the default) or "f64" (native FP64)."""
 
-    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int):
+    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff"):
         import torch
         if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
             raise ValueError("nsteps must be a positive multiple of ckpt")
@@ -47,7 +48,10 @@ class WidthGradient:
         self.lat = lat
         self.N = int(nsteps)
         self.K = int(ckpt)
-        self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64")
+        if prec not in ("f64", "f64_ff"):
+            raise ValueError("the adjoint needs FP64 storage (prec 'f64' or 'f64_ff')")
+        self.prec = prec
+        self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
         self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]

@@ -1,0 +1,331 @@
+// adjoint_ff.cuh -- the adjoint step lam_t = P^T J_C(g)^T lam_{t+1} (adjoint.cuh) with
+// binary64 storage and an FP64-accurate float-float evaluation, the transpose of the
+// float-float collide of step_ff.cuh.
+//
+// Per site, with D = 2, u the velocity and T the temperature of the pulled g = P f_t,
+// u_s = u + tau g_vec, th = T_s - 1 (the shifted equilibrium of Sec. III.A), and
+// P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 the equilibrium polynomial of one velocity
+// (s = xi . u_s, K0..K2 polynomials in |u_s|^2, th and C2 = |xi|^2):
+//   A  = sum_l w_l lam_l P_l,          B  = sum_l w_l lam_l dP/ds_l xi_l,
+//   Bu = sum_l w_l lam_l dP/du2_l,     Cs = sum_l w_l lam_l dP/dth_l,
+//   Bt = B + 2 Bu u_s,   A' = A - Bt . u + Cs (|u|^2 / 2 - T),   B' = Bt - Cs u,   C' = Cs / 2,
+//   lam_t(source of l) = (1 - w) lam_l + w (A' + B' . xi_l + C' |xi_l|^2)
+// (rho cancels between df^eq/dM and dM/dg).  The even/odd split of a velocity pair
+// (ls = lam_A + lam_B, ld = lam_A - lam_B) and dP/du2 = -(K1 + s + q/2) / 2 (q = s^2;
+// K1 = -2 dK0/du2) give, with the factor 24 of step_ff.cuh folded into the K:
+//   24 A        = sum w [ls (24K0 + q (24K2 + q)) + ld s (24K1 + 4 q)]
+//   24 B / r    = sum w c [ld (24K1 + 12 q) + 2 ls s (24K2 + 2 q)]
+//   -48 Bu      = sum w [ls (24K1 + 12 q) + 24 ld s]
+//   4 Cs        = sum w [ls (4 H0 + (C2 - 6) q) + 2 (C2 - 4) ld s],  H0 = dK0/dth.
+// Numerics: lam_{t+1} is taken apart into float-float with integer instructions after
+// scaling by the site's block exponent (the largest exponent among its 37 values), so the
+// relative accuracy does not depend on the magnitude of lam; the moments of g come from the
+// 64-bit fixed-point sums of step_ff.cuh; the result A' + B'.xi + C'|xi|^2 (scaled back by
+// the block exponent) enters the binary64 output through one FP64 FMA per population.
+// FP64 instructions per site: the 37 FMAs, and the five conversions of the moments.
+#pragma once
+#include "step_ff.cuh"
+
+namespace lbm {
+
+struct AdjParamsFF {
+    int Lx, Lz, plane;
+    double one_m_omega_d;
+    ff3 wsh[NSHELL];       // omega w_shell
+    ff us_z, T_shift;      // tau (-g), tau (1 - tau) g^2 / D
+    ff3 r2, r4;            // r^2, r^4
+    ff3 r_24, inv24;       // r / 24, 1 / 24
+    ff c6[NSHELL];         // r^2 |c|^2 - 6 of each shell
+    ff c4[NSHELL];         // 2 (r^2 |c|^2 - 4)
+};
+
+// a * c, not renormalised.
+__device__ __forceinline__ ff ff_mul_c3_u(ff a, const ff3& c) {
+    const float p = a.hi * c.hi;
+    float e = fmaf(a.hi, c.hi, -p);
+    e = fmaf(a.hi, c.lo2, e);
+    e = fmaf(a.hi, c.lo, e);
+    e = fmaf(a.lo, c.hi, e);
+    return ff{p, e};
+}
+
+// a + 2 b when |a| >= |2 b| is known, not renormalised.
+__device__ __forceinline__ ff ff_add_big_u_x2(ff a, ff b) {
+    const float s = fmaf(2.0f, b.hi, a.hi);
+    const float e = fmaf(2.0f, b.hi, -(s - a.hi));
+    return ff{s, e + fmaf(2.0f, b.lo, a.lo)};
+}
+
+// Renormalisation without an ordering assumption (the sum may have cancelled).
+__device__ __forceinline__ ff ff_renorm2(ff a) { return two_sum(a.hi, a.lo); }
+
+// binary64 bit pattern of x -> float-float of x * 2^-(S >> 20), S = (E_block - 1023) << 20 a
+// signed shift of the exponent field.  The value after scaling must stay below 2^127 in
+// magnitude; values that fall below 2^-74 after scaling come out as 0 (as do zero and the
+// subnormals, which have no exponent, as long as E_block >= 75).
+__device__ __forceinline__ ff bits_to_ff_scaled(uint32_t H, uint32_t L, int32_t S) {
+    const uint32_t sgn = H & 0x80000000u;
+    const int32_t Ha = (int32_t)(H & 0x7FFFFFFFu) - S;
+    const bool ok = Ha >= (int32_t)(949u << 20);
+    const uint32_t Hu = (uint32_t)Ha;
+    const uint64_t m = ((((uint64_t)Hu) << 32) | L) + 0x10000000ull;
+    const uint32_t hb = (uint32_t)(m >> 29) - 0xC0000000u;
+    const int32_t rem = ((int32_t)(L << 3)) >> 3;
+    const uint32_t sb = (Hu >> 20) * 0x00800000u + 0x26000000u;
+    const float hi = __uint_as_float(ok ? (hb | sgn) : 0u);
+    const float lo = (float)rem * __uint_as_float(ok ? (sb | sgn) : 0u);   // sb may be Inf when !ok
+    return ff{hi, lo};
+}
+
+// Normalised float-float a -> binary64 of a * 2^(S >> 20) (ff_to_double_bits with the
+// exponent field moved by S, S >= (75 - 1023) << 20); 0 when |a.hi| < 2^-74, the range in
+// which the assembly's scale 2^(52 - e) would leave FP32 (such a result lies below 2^-74 of
+// the block scale; every other result lands in the binary64 normal range).
+__device__ __forceinline__ double ff_to_double_scaled(ff a, int32_t S) {
+    const uint32_t hb = __float_as_uint(a.hi);
+    const uint32_t ha = hb & 0x7FFFFFFFu;
+    const uint32_t sgn = hb & 0x80000000u;
+    const uint32_t PH = (ha >> 3) + (896u << 20) + (uint32_t)S + sgn;
+    const uint32_t PL = ha << 29;
+    const uint32_t m = (uint32_t)((int32_t)(__float_as_uint(a.lo) ^ hb) >> 31);
+    const uint32_t sbits = 0x99000000u - ((hb + m) & 0x7F800000u) + sgn;
+    const int32_t k = __float2int_rn(a.lo * __uint_as_float(sbits));
+    const uint64_t P = ((((uint64_t)PH) << 32) | PL) + (uint64_t)(int64_t)k;
+    return __longlong_as_double(ha >= (53u << 23) ? (long long)P : 0ll);
+}
+
+// lam_{t+1} at the site itself: the high words (block exponent) and the values.
+struct LamOwn {
+    const double* __restrict__ lam;
+    int o, plane;
+    template <int L>
+    __device__ __forceinline__ uint32_t hiword() const {
+        uint32_t v;
+        const double* p = lam + LBM_IDX(L * plane + o, Q * plane);
+        asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"((const char*)p + 4));
+        return v;
+    }
+    template <int L>
+    __device__ __forceinline__ double again() const { return LoadNC::ld_again(lam + LBM_IDX(L * plane + o, Q * plane)); }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
+        va = LoadNC::ld_again(lam + LBM_IDX(pi.A * plane + o, Q * plane));
+        vb = LoadNC::ld_again(lam + LBM_IDX(pi.B * plane + o, Q * plane));
+    }
+};
+
+// The adjoint's results go to the pull source of each population (P^T: the inverse of the
+// gather, unique targets because propagate + bc is a permutation).
+template <bool WALL>
+struct DstSource {
+    double* __restrict__ out;
+    const SiteAddr& ad;
+    const int* sbase;
+    template <int L>
+    __device__ __forceinline__ void put(double v) const {
+        if constexpr (WALL) out[LBM_IDX((ad.template src<L, true>()), Q * ad.plane)] = v;
+        else out[LBM_IDX(sbase[L] + ad.z, Q * ad.plane)] = v;
+    }
+    __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
+        if constexpr (WALL) {
+            out[LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane)] = va;
+            out[LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane)] = vb;
+        } else {
+            out[LBM_IDX(sbase[pi.A] + ad.z, Q * ad.plane)] = va;
+            out[LBM_IDX(sbase[pi.B] + ad.z, Q * ad.plane)] = vb;
+        }
+    }
+};
+
+// Running float-float sums (unnormalised) of the pair loop.
+struct AdjSums {
+    ff A, Bx, Bz, U, C;
+};
+
+template <class FSRC, class DST>
+__device__ __forceinline__ void adjoint_site_ff(const FSRC& fsrc, const LamOwn& lsrc, const DST& dst,
+                                                const AdjParamsFF& p) {
+    // -- pass 1: moments of the pulled f_t; block exponent of lam_{t+1} -----------------
+    const MomentsFix m = moments_ff(fsrc);
+    uint32_t eb = 75u << 20;      // floor: zero and subnormal lam stay 0 after scaling
+    static_for<Q>([&](auto l) { eb = max(eb, lsrc.template hiword<decltype(l)::value>() & 0x7FF00000u); });
+    const int32_t S = (int32_t)eb - (int32_t)(1023u << 20);                  // (E_block - 1023) << 20
+    // -- per-site scalars in float-float (as in collide_ff) ------------------------------
+    const double Rd = __ll2double_rn(m.R);
+    const ff rho = dsplit(Rd), jx = i64_to_ff(m.Jx), jz = i64_to_ff(m.Jz);
+    const ff dT = dsplit(fma(d_lat.r2_half, __ll2double_rn(m.E), -Rd));
+    const ff inv = ff_rcp(rho);
+    const ff3 r = ff3_of(d_lat.r3);
+    const ff rinv = ff_mul_c3(inv, r);
+    const ff ux = ff_mul(jx, rinv), uz = ff_mul(jz, rinv);
+    const ff usz = ff_add(uz, p.us_z);
+    const ff ux2 = ff_mul_u(ux, ux);
+    const ff u2 = ff_add(ux2, ff_mul_u(usz, usz));                         // |u_s|^2
+    const ff uu = ff_add(ux2, ff_mul_u(uz, uz));                           // |u|^2
+    const ff tm1 = ff_sub(ff_mul_u(dT, inv), ff_mul_pow2(uu, 0.5f));        // T - 1
+    const ff th = ff_add(tm1, p.T_shift);
+    const ff a = ff_mul_c3(ux, r), b = ff_mul_c3(usz, r);
+    // -- 24 K0, 24 K1, 24 K2 and 4 H0 as polynomials in |c|^2 ------------------------------
+    const ff th2 = ff_mul(th, th), thu2 = ff_mul(th, u2), u4 = ff_mul_u(u2, u2);
+    const ff k00 = ff_add(ff_add(ff_make(24.0f, 0.0f), ff_mul_f_u(u2, -12.0f)),
+                          ff_add(ff_mul_f_u(u4, 3.0f), ff_mul_f_u(ff_add(thu2, ff_sub(th2, th)), 24.0f)));
+    const ff k01 = ff_mul_c3(ff_sub(ff_mul_pow2(th, 2.0f), ff_add(thu2, ff_mul_pow2(th2, 4.0f))), ff3_of(d_lat.r2x6));
+    const ff k02 = ff_mul_c3(th2, ff3_of(d_lat.r4x3));
+    const ff k10 = ff_add(ff_make(24.0f, 0.0f), ff_add(ff_mul_f_u(u2, -12.0f), ff_mul_f_u(th, -48.0f)));
+    const ff k11 = ff_mul_c3(th, ff3_of(d_lat.r2x12));
+    const ff k20 = ff_add(ff_make(12.0f, 0.0f), ff_add(ff_mul_f_u(u2, -6.0f), ff_mul_f_u(th, -36.0f)));
+    const ff k21 = ff_mul_c3(th, ff3_of(d_lat.r2x6));
+    // 4 H0 = (-4 + 4 u2 + 8 th) + r^2 (2 - u2 - 8 th) |c|^2 + r^4 th |c|^4
+    const ff h00 = ff_add(ff_make(-4.0f, 0.0f), ff_add(ff_mul_pow2(u2, 4.0f), ff_mul_pow2(th, 8.0f)));
+    const ff h01 = ff_mul_c3(ff_sub(ff_make(2.0f, 0.0f), ff_add(u2, ff_mul_pow2(th, 8.0f))), p.r2);
+    const ff h02 = ff_mul_c3(th, p.r4);
+    // -- pass 2: the sums ------------------------------------------------------------------
+    AdjSums sm;
+    {
+        const double v0 = lsrc.template again<0>();
+        const ff l0 = ff_mul_c3_u(bits_to_ff_scaled((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0), S),
+                                  p.wsh[0]);
+        sm.A = ff_mul_u(l0, k00);       // s = 0, |c|^2 = 0
+        sm.U = ff_mul_u(l0, k10);
+        sm.C = ff_mul_u(l0, h00);
+        sm.Bx = ff_make(0.0f, 0.0f);
+        sm.Bz = ff_make(0.0f, 0.0f);
+    }
+    auto pair_sums = [&](const PairInfo& pi, const ff& K0, const ff& K1, const ff& K2, const ff& H,
+                         const ff3& W, const ff& c6, const ff& c4, double va, double vb) {
+        const ff la = bits_to_ff_scaled((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va), S);
+        const ff lb = bits_to_ff_scaled((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb), S);
+        const ff ls = ff_mul_c3_u(ff_add_u(la, lb), W);
+        const ff ld = ff_mul_c3_u(ff_add_u(la, ff_neg(lb)), W);
+        const ff sx = ff_mul_f_u(a, pi.fcx), sz = ff_mul_f_u(b, pi.fcz);
+        const ff st = two_sum(sx.hi, sz.hi);
+        const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
+        const ff q = ff_mul_u(s, s);
+        const ff P1 = ff_mul_u(ld, s), P2 = ff_mul_u(ls, s);
+        const ff ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, q)));     // 24 K0 + q (24 K2 + q)
+        const ff od = ff_add_big_u_x4(K1, q);                                 // 24 K1 + 4 q
+        const ff e1 = ff_add_big_u(K1, ff_mul_f_u(q, 12.0f));                 // 24 K1 + 12 q
+        const ff t2 = ff_add_big_u_x2(K2, q);                                 // 24 K2 + 2 q
+        sm.A = ff_add_u(sm.A, ff_add_u(ff_mul_u(ls, ev), ff_mul_u(P1, od)));
+        const ff bt = ff_add_u(ff_mul_u(ld, e1), ff_mul_pow2(ff_mul_u(P2, t2), 2.0f));
+        sm.Bx = ff_add_u(sm.Bx, ff_mul_f_u(bt, pi.fcx));
+        sm.Bz = ff_add_u(sm.Bz, ff_mul_f_u(bt, pi.fcz));
+        sm.U = ff_add_u(sm.U, ff_add_u(ff_mul_u(ls, e1), ff_mul_f_u(P1, 24.0f)));
+        const ff hq = ff_add_big_u(H, ff_mul_u(c6, q));
+        sm.C = ff_add_u(sm.C, ff_add_u(ff_mul_u(ls, hq), ff_mul_u(c4, P1)));
+    };
+#pragma unroll 1
+    for (int sh = 1; sh < NSHELL; sh++) {
+        const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
+        const float C2 = d_pairs[k0].fc2;
+        const ff K0 = ff_add_u(k00, ff_mul_f_u(ff_add_u(k01, ff_mul_f_u(k02, C2)), C2));
+        const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
+        const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
+        const ff H = ff_add_u(h00, ff_mul_f_u(ff_add_u(h01, ff_mul_f_u(h02, C2)), C2));
+        const ff3 W = p.wsh[sh];
+        const ff c6 = p.c6[sh], c4 = p.c4[sh];
+#pragma unroll 1
+        for (int k = k0; k < k1; k += 2) {
+            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
+            double v0a, v0b, v1a, v1b;
+            lsrc.pair(p0, v0a, v0b);
+            lsrc.pair(p1, v1a, v1b);
+            pair_sums(p0, K0, K1, K2, H, W, c6, c4, v0a, v0b);
+            pair_sums(p1, K0, K1, K2, H, W, c6, c4, v1a, v1b);
+        }
+    }
+    // -- A', B', C' (times omega, in units of the block exponent) ---------------------------
+    const ff A = ff_mul_c3(ff_renorm2(sm.A), p.inv24);
+    const ff Bx = ff_mul_c3(ff_renorm2(sm.Bx), p.r_24), Bz = ff_mul_c3(ff_renorm2(sm.Bz), p.r_24);
+    const ff Bu = ff_mul_pow2(ff_mul_c3(ff_renorm2(sm.U), p.inv24), -0.5f);
+    const ff Cs = ff_mul_pow2(ff_renorm2(sm.C), 0.25f);
+    const ff Btx = ff_add(Bx, ff_mul_pow2(ff_mul(Bu, ux), 2.0f));
+    const ff Btz = ff_add(Bz, ff_mul_pow2(ff_mul(Bu, usz), 2.0f));
+    // |u|^2 / 2 - T with T = 1 + tm1
+    const ff tq = ff_sub(ff_mul_pow2(uu, 0.5f), ff_add(ff_make(1.0f, 0.0f), tm1));
+    const ff Ap = ff_add(ff_sub(A, ff_add(ff_mul(Btx, ux), ff_mul(Btz, uz))), ff_mul(Cs, tq));
+    const ff phx = ff_mul_c3(ff_sub(Btx, ff_mul(Cs, ux)), r);                // r B'_x
+    const ff phz = ff_mul_c3(ff_sub(Btz, ff_mul(Cs, uz)), r);                // r B'_z
+    const ff ph2 = ff_mul_pow2(ff_mul_c3(Cs, p.r2), 0.5f);                   // r^2 C'
+    // -- pass 3: lam_t = (1 - w) lam + w (A' + B'.xi + C'|xi|^2), to the pull sources -------
+    {
+        const double v0 = lsrc.template again<0>();
+        dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_scaled(Ap, S)));
+    }
+#pragma unroll 1
+    for (int sh = 1; sh < NSHELL; sh++) {
+        const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
+        const ff ev = ff_add_u(Ap, ff_mul_f_u(ph2, d_pairs[k0].fc2));
+#pragma unroll 1
+        for (int k = k0; k < k1; k += 2) {
+            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
+            double v0a, v0b, v1a, v1b;
+            lsrc.pair(p0, v0a, v0b);
+            lsrc.pair(p1, v1a, v1b);
+            auto out = [&](const PairInfo& pi, double va, double vb) {
+                const ff ox = ff_mul_f_u(phx, pi.fcx), oz = ff_mul_f_u(phz, pi.fcz);
+                const ff ot = two_sum(ox.hi, oz.hi);
+                const ff od = ff_make(ot.hi, ot.lo + (ox.lo + oz.lo));
+                const double Xa = ff_to_double_scaled(ff_renorm2(ff_add_u(ev, od)), S);
+                const double Xb = ff_to_double_scaled(ff_renorm2(ff_add_u(ev, ff_neg(od))), S);
+                dst.pair(pi, fma(p.one_m_omega_d, va, Xa), fma(p.one_m_omega_d, vb, Xb));
+            };
+            out(p0, v0a, v0b);
+            out(p1, v1a, v1b);
+        }
+    }
+}
+
+// One tile b of the tiling t (the step's tiling: wall tiles, then interior columns).
+__device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const double* __restrict__ lam_next,
+                                                double* __restrict__ lam_out, const AdjParamsFF& p, Tiling t,
+                                                int b, int* sbase) {
+    const bool wall_tile = tile_is_wall(t, b);
+    if (!wall_tile) {
+        fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+        __syncthreads();
+    }
+    SiteAddr ad;
+    bool wall;
+    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+    const LamOwn lsrc{lam_next, ad.dst(), p.plane};
+    if (wall)
+        adjoint_site_ff(SrcGlobal<true, LoadNC>{ft, ad, sbase}, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
+    else
+        adjoint_site_ff(SrcGlobal<false, LoadNC>{ft, ad, sbase}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
+}
+
+__global__ void __launch_bounds__(BLOCK_Z, 4)
+k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
+             AdjParamsFF p, Tiling t) {
+    __shared__ int sbase[Q];
+    adjoint_tile_ff(ft, lam_next, lam_out, p, t, blockIdx.x, sbase);
+}
+
+// w_shell: the shell weights; r: the lattice constant (both binary64).
+inline AdjParamsFF adj_ff_params(const StepParams& p, const double* w_shell, double r) {
+    AdjParamsFF q;
+    q.Lx = p.Lx; q.Lz = p.Lz; q.plane = p.plane;
+    q.one_m_omega_d = p.one_m_omega;
+    const long double rl = r, r2 = rl * rl;
+    for (int sh = 0; sh < NSHELL; sh++) {
+        q.wsh[sh] = ff3_host((long double)p.omega * w_shell[sh]);
+        const long double C2 = r2 * shell_c2(sh);
+        q.c6[sh] = ff_host((double)(C2 - 6.0L));
+        q.c4[sh] = ff_host((double)(2.0L * (C2 - 4.0L)));
+    }
+    q.us_z = ff_host(p.us_z);
+    q.T_shift = ff_host(p.T_shift);
+    q.r2 = ff3_host(r2);
+    q.r4 = ff3_host(r2 * r2);
+    q.r_24 = ff3_host(rl / 24.0L);
+    q.inv24 = ff3_host(1.0L / 24.0L);
+    return q;
+}
+
+inline void launch_adjoint_ff(const double* ft, const double* lam_next, double* lam_out, const StepParams& p,
+                              const double* w_shell, double r, const Tiling& t, cudaStream_t st) {
+    const AdjParamsFF q = adj_ff_params(p, w_shell, r);
+    k_adjoint_ff<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+}
+
+}  // namespace lbm

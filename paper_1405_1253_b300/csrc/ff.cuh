@@ -134,7 +134,9 @@ __device__ __forceinline__ ff bits_to_ff(uint32_t H, uint32_t L) {
     const uint32_t sb = (Ha >> 20) * 0x00800000u + 0x26000000u;
     const bool ok = Ha >= (949u << 20);                              // |x| >= 2^-74
     const float hi = __uint_as_float(ok ? (hb | sgn) : 0u);
-    const float lo = (float)(ok ? rem : 0) * __uint_as_float(sb | sgn);
+    // the scale is selected, not rem: for |x| < 2^-74 the pattern sb is meaningless (in some
+    // binades an infinity, whose product with 0 would be a NaN)
+    const float lo = (float)rem * __uint_as_float(ok ? (sb | sgn) : 0u);
     return ff{hi, lo};
 }
 

@@ -21,6 +21,7 @@
 #include "step_f32.cuh"
 #include "init_diag.cuh"
 #include "adjoint.cuh"
+#include "adjoint_ff.cuh"
 #include "ensemble.cuh"
 
 using namespace lbm;
@@ -734,19 +735,24 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
 // ---------------------------------------------------------------------------------
 int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
     if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
-    dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
-    k_adjoint_f64<<<grid, BLOCK_Z, 0, c->stream>>>(f_t, lam_next, lam_out, p);
+    if (c->prec == LBM_F64_FF) {
+        launch_adjoint_ff(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z),
+                          c->stream);
+    } else {
+        dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
+        k_adjoint_f64<<<grid, BLOCK_Z, 0, c->stream>>>(f_t, lam_next, lam_out, p);
+    }
     LAUNCH_CHECK();
     return LBM_OK;
 }
 
 int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double* lam_out) {
     if (!c || !f || !dL_dTbar || !lam_out) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     DeviceGuard dg(c->device);
     CU(cudaMemcpyAsync(c->dLrow, dL_dTbar, (size_t)c->Lz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     dim3 grid((c->Lz + 127) / 128, c->Lx);
@@ -758,7 +764,7 @@ int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double
 
 int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi) {
     if (!c || !lam0) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec != LBM_F64) return fail(LBM_ESTATE, "the adjoint needs an LBM_F64 context");
+    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     DeviceGuard dg(c->device);
     InitParams ip;
     int rc = fill_init_params(c, d, &ip);

@@ -52,12 +52,13 @@ def exercise():
             E.step(3)
             E.sync()
         E.close()
-    A = lbm.Lattice(12, 48, 0.8, 1e-3, prec="f64")
-    A.init_from(W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=23))
-    f = A.populations_device().clone()
-    lam = torch.rand_like(f)
-    out = torch.empty_like(f)
-    A.adjoint_step(f, lam, out)
+    for prec in ("f64", "f64_ff"):
+        A = lbm.Lattice(12, 48, 0.8, 1e-3, prec=prec)
+        A.init_from(W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=23))
+        f = A.populations_device().clone()
+        lam = torch.rand_like(f)
+        out = torch.empty_like(f)
+        A.adjoint_step(f, lam, out)
     H = lbm.Lattice(16, 48, 0.8, 1e-4, prec="f64_ff")
     a = np.ones(37 * 16 * 48)
     b = np.empty_like(a)

@@ -16,10 +16,11 @@ def adj():
     return adjoint
 
 
-def test_gradient_matches_oracle_chain(adj):
+@pytest.mark.parametrize("prec", ["f64", "f64_ff"])
+def test_gradient_matches_oracle_chain(adj, prec):
     lat = W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=21)
     nsteps, ckpt = 6, 3
-    drv = adj.WidthGradient(lat, nsteps, ckpt)
+    drv = adj.WidthGradient(lat, nsteps, ckpt, prec=prec)
     m = lat.modes()
     Lval = drv.forward(m.amp_lo, m.amp_hi)
     g_lo, g_hi = drv.backward()
