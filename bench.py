@@ -51,6 +51,7 @@ KERNEL_SOURCES = {
     "k_step_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh"),
     "k_step_f64": ("lattice.cuh", "common.cuh", "step_f64.cuh"),
     "k_step_f32": ("lattice.cuh", "common.cuh", "step_f32.cuh"),
+    "k_adjoint_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
 }
 
 
@@ -347,6 +348,7 @@ def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
         L.close()
         gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
         out[prec] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+    out["f64_ff"]["traffic"] = ncu_traffic("k_adjoint_ff", lat.sites)
     return out
 
 

@@ -21,8 +21,8 @@
 // scaling by the site's block exponent (the largest exponent among its 37 values), so the
 // relative accuracy does not depend on the magnitude of lam; the moments of g come from the
 // 64-bit fixed-point sums of step_ff.cuh; the result A' + B'.xi + C'|xi|^2 (scaled back by
-// the block exponent) enters the binary64 output through one FP64 FMA per population.
-// FP64 instructions per site: the 37 FMAs, and the five conversions of the moments.
+// the block exponent) enters the binary64 output through FP64 adds and one FP64 FMA per
+// population.  FP64 instructions per site: 37 FMAs, 36 adds, the five moment conversions.
 #pragma once
 #include "step_ff.cuh"
 
@@ -251,10 +251,13 @@ __device__ __forceinline__ void adjoint_site_ff(const FSRC& fsrc, const LamOwn& 
         const double v0 = lsrc.template again<0>();
         dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_scaled(Ap, S)));
     }
+    // even part A' + C'|xi|^2 once per shell, odd part B'.xi once per pair, each rounded to
+    // binary64; the sum and the relaxation are FP64 (the FP64 pipe has room for the adds,
+    // the issue slots of a float-float add and a second assembly per population it saves)
 #pragma unroll 1
     for (int sh = 1; sh < NSHELL; sh++) {
         const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
-        const ff ev = ff_add_u(Ap, ff_mul_f_u(ph2, d_pairs[k0].fc2));
+        const double ev = ff_to_double_scaled(ff_renorm2(ff_add_u(Ap, ff_mul_f_u(ph2, d_pairs[k0].fc2))), S);
 #pragma unroll 1
         for (int k = k0; k < k1; k += 2) {
             const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
@@ -264,10 +267,8 @@ __device__ __forceinline__ void adjoint_site_ff(const FSRC& fsrc, const LamOwn& 
             auto out = [&](const PairInfo& pi, double va, double vb) {
                 const ff ox = ff_mul_f_u(phx, pi.fcx), oz = ff_mul_f_u(phz, pi.fcz);
                 const ff ot = two_sum(ox.hi, oz.hi);
-                const ff od = ff_make(ot.hi, ot.lo + (ox.lo + oz.lo));
-                const double Xa = ff_to_double_scaled(ff_renorm2(ff_add_u(ev, od)), S);
-                const double Xb = ff_to_double_scaled(ff_renorm2(ff_add_u(ev, ff_neg(od))), S);
-                dst.pair(pi, fma(p.one_m_omega_d, va, Xa), fma(p.one_m_omega_d, vb, Xb));
+                const double od = ff_to_double_scaled(ff_renorm2(ff_make(ot.hi, ot.lo + (ox.lo + oz.lo))), S);
+                dst.pair(pi, fma(p.one_m_omega_d, va, ev + od), fma(p.one_m_omega_d, vb, ev - od));
             };
             out(p0, v0a, v0b);
             out(p1, v1a, v1b);

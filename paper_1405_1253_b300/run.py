@@ -1,6 +1,8 @@
-"""Command-line runner: initialise a three-layer lattice and advance it.
+"""Command-line runner: initialise a three-layer lattice and advance it; optionally apply
+the adjoint step to a seeded random field at the final state (FP64 storage only).
 
   python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
+  python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3
 
 Used as the profiled program of the ncu summaries under profiles/.
 """
@@ -23,6 +25,7 @@ def main():
     ap.add_argument("--sigma", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--adjoint", type=int, default=0, help="adjoint steps after the forward steps")
     args = ap.parse_args()
     from . import lbm
     lat = W.Lattice(args.Lx, args.Lz, tau=args.tau, grav=args.grav, K=args.modes, sigma=args.sigma, seed=args.seed)
@@ -31,8 +34,17 @@ def main():
     L.step(args.steps)
     L.sync()
     mass, energy = L.global_sums()
-    print(json.dumps({"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "mass": mass,
-                      "energy": energy}))
+    out = {"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "mass": mass, "energy": energy}
+    if args.adjoint > 0:
+        import torch
+        f = L.populations_device().clone()
+        gen = torch.Generator(device=f.device).manual_seed(args.seed)
+        lam = [torch.rand(f.numel(), dtype=torch.float64, device=f.device, generator=gen), torch.empty_like(f)]
+        for i in range(args.adjoint):
+            L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+        L.sync()
+        out.update(adjoint_steps=args.adjoint, lam_sum=float(lam[args.adjoint & 1].sum()))
+    print(json.dumps(out))
     L.close()
 
 
