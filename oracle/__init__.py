@@ -63,6 +63,8 @@ def _load():
                 "oracle_site_moments": (None, [dp, dp]),
                 "oracle_propagate": (None, [i, i, dp, dp]),
                 "oracle_bc": (None, [i, i, dp, dp]),
+                "oracle_bc_thermal": (None, [i, i, dp, dp, d, d]),
+                "oracle_step_thermal": (None, [i, i, d, d, i, dp, dp, d, d]),
                 "oracle_collide": (None, [i, i, d, d, dp, dp]),
                 "oracle_step": (None, [i, i, d, d, i, dp, dp]),
                 "oracle_init_layers": (None, [i, i, d, d, d, d, d, d, d, d, i, dp, dp, dp, dp, dp]),
@@ -148,6 +150,16 @@ def bc(f: np.ndarray, g: np.ndarray) -> np.ndarray:
     return g
 
 
+def bc_thermal(f: np.ndarray, g: np.ndarray, T_bot: float, T_top: float) -> np.ndarray:
+    """Thermal-wall variant of bc: ghost rows at rest at T_bot / T_top, mass-balanced."""
+    lib = _load()
+    f = _f64(f)
+    g = _f64(g).copy()
+    _, Lx, Lz = f.shape
+    lib.oracle_bc_thermal(Lx, Lz, _p(f), _p(g), float(T_bot), float(T_top))
+    return g
+
+
 def collide(g: np.ndarray, tau: float, grav: float) -> np.ndarray:
     lib = _load()
     g = _f64(g)
@@ -157,12 +169,17 @@ def collide(g: np.ndarray, tau: float, grav: float) -> np.ndarray:
     return out
 
 
-def step(f: np.ndarray, tau: float, grav: float, nsteps: int = 1) -> np.ndarray:
+def step(f: np.ndarray, tau: float, grav: float, nsteps: int = 1, walls=None) -> np.ndarray:
+    """nsteps full steps; walls=None: bounce-back walls, walls=(T_bot, T_top): thermal walls."""
     lib = _load()
     f = _f64(f).copy()
     _, Lx, Lz = f.shape
     work = np.empty_like(f)
-    lib.oracle_step(Lx, Lz, float(tau), float(grav), int(nsteps), _p(f), _p(work))
+    if walls is None:
+        lib.oracle_step(Lx, Lz, float(tau), float(grav), int(nsteps), _p(f), _p(work))
+    else:
+        lib.oracle_step_thermal(Lx, Lz, float(tau), float(grav), int(nsteps), _p(f), _p(work),
+                                float(walls[0]), float(walls[1]))
     return f
 
 

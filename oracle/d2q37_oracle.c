@@ -375,6 +375,62 @@ void oracle_bc(int Lx, int Lz, const double *f, double *g) {
 }
 
 /* ---------------------------------------------------------------------------
+ * Thermal-wall variant of the bc (Sec. III.B names only the rows).  Reading: each wall is
+ * an isothermal no-slip wall at temperature T_w, realised by three ghost rows beyond it
+ * (z = -1, -2, -3 below the bottom, Lz, Lz+1, Lz+2 above the top) that hold the
+ * equilibrium at rest f^eq(rho_w(x), 0, T_w).  A destination whose pull source row lies
+ * in a ghost row takes that ghost population.  The ghost density of each ghost column x
+ * balances the mass through the wall in the step:
+ *   out(x) = sum of the populations f_l(x', z) whose move z + c_lz, x' + c_lx (mod Lx)
+ *            lands in a ghost row of column x;
+ *   in(x)  = rho_w(x) * sum over ghost rows zg and velocities l of f^eq_l(1, 0, T_w) for
+ *            which zg + c_lz lies inside the lattice;
+ *   rho_w(x) = out(x) / in(x) at rho_w = 1,
+ * so the total mass is conserved exactly and the wall sends the fluid a Maxwellian at
+ * its own temperature.
+ * ------------------------------------------------------------------------- */
+static void thermal_wall(int Lx, int Lz, const double *f, double *g, double Tw, int top) {
+    double feq1[NPOP];
+    equilibrium_with_derivs(1.0, 0.0, 0.0, Tw, feq1, NULL, NULL);
+    const int g0 = top ? Lz : -3;                       /* ghost rows g0 .. g0 + 2 */
+    double in1 = 0.0;                                   /* inflow per unit ghost density */
+    for (int zg = g0; zg < g0 + 3; zg++)
+        for (int l = 0; l < NPOP; l++) {
+            int zd = zg + VEL[l][1];
+            if (zd >= 0 && zd < Lz) in1 += feq1[l];
+        }
+    double *out = calloc((size_t)Lx, sizeof(double));
+    for (int x = 0; x < Lx; x++)
+        for (int z = 0; z < Lz; z++)
+            for (int l = 0; l < NPOP; l++) {
+                int zd = z + VEL[l][1];
+                if (zd >= g0 && zd < g0 + 3) {
+                    int xd = ((x + VEL[l][0]) % Lx + Lx) % Lx;
+                    out[xd] += f[ix(Lx, Lz, l, x, z)];
+                }
+            }
+    for (int x = 0; x < Lx; x++)
+        for (int l = 0; l < NPOP; l++)
+            for (int z = 0; z < Lz; z++) {
+                int zs = z - VEL[l][1];
+                if (zs < g0 || zs >= g0 + 3) continue;
+                int xs = ((x - VEL[l][0]) % Lx + Lx) % Lx;
+                g[ix(Lx, Lz, l, x, z)] = out[xs] / in1 * feq1[l];
+            }
+    free(out);
+}
+
+void oracle_bc_thermal(int Lx, int Lz, const double *f, double *g, double T_bot, double T_top) {
+    oracle_setup();
+    thermal_wall(Lx, Lz, f, g, T_bot, 0);
+    thermal_wall(Lx, Lz, f, g, T_top, 1);
+}
+
+/* One full step with the thermal walls: f <- collide(bc_thermal(propagate(f))). */
+void oracle_step_thermal(int Lx, int Lz, double tau, double grav, int nsteps, double *f, double *work,
+                         double T_bot, double T_top);
+
+/* ---------------------------------------------------------------------------
  * Collide (Sec. III.A, Eq. (LBE) right-hand side with the shifted equilibrium):
  *   f'_l = g_l - (1/tau) [g_l - f^eq_l(rho, u + tau gvec, T + tau (1 - tau) g^2 / D)]
  * with rho, u, T the moments of the post-propagate g, gvec = (0, -grav), dt = 1.
@@ -401,6 +457,16 @@ void oracle_step(int Lx, int Lz, double tau, double grav, int nsteps, double *f,
     for (int s = 0; s < nsteps; s++) {
         oracle_propagate(Lx, Lz, f, work);
         oracle_bc(Lx, Lz, f, work);
+        oracle_collide(Lx, Lz, tau, grav, work, f);
+    }
+}
+
+void oracle_step_thermal(int Lx, int Lz, double tau, double grav, int nsteps, double *f, double *work,
+                         double T_bot, double T_top) {
+    oracle_setup();
+    for (int s = 0; s < nsteps; s++) {
+        oracle_propagate(Lx, Lz, f, work);
+        oracle_bc_thermal(Lx, Lz, f, work, T_bot, T_top);
         oracle_collide(Lx, Lz, tau, grav, work, f);
     }
 }
