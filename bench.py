@@ -352,6 +352,30 @@ def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
     return out
 
 
+def bench_walls(torch, lbm, lat, steps, stream):
+    """Thermal walls (lbm_set_walls: two launches per step) against the bounce-back step on
+    the 1024x2048 state, float-float and FP32 storage."""
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps, walls at T_d / T_u"}
+    for prec in ("f64_ff", "f32"):
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        res = {}
+        for thermal in (False, True):
+            L.set_walls(thermal, lat.T_d, lat.T_u)
+            L.step(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            res["thermal" if thermal else "bounce_back"] = lat.sites * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+        L.close()
+        out[prec] = {"bounce_back_mlups": res["bounce_back"], "thermal_mlups": res["thermal"],
+                     "thermal_over_bounce_back": res["thermal"] / res["bounce_back"]}
+    return out
+
+
 def fp32_error(torch, lbm, lat, steps, stream):
     """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
     step after `steps` steps from the same initial state."""
@@ -441,6 +465,7 @@ def run_ours(args):
                                                         float(measured_peaks()[0].get("hbm_gbs", 6400.0)))
         extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
         extras["push_vs_pull"] = bench_push(torch, lbm, lat, 200, stream)
+        extras["walls"] = bench_walls(torch, lbm, lat, 200, stream)
 
     if rank != 0:
         return

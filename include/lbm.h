@@ -106,6 +106,19 @@ int lbm_init_layers(lbm_ctx *c, const lbm_layers_desc *d);
  * kernel launch per step, ping-ponging between the two buffers.  Asynchronous.       */
 int lbm_step(lbm_ctx *c, int nsteps);
 
+/* Wall rule of lbm_step and lbm_step_host (Sec. III.B names only the bc rows 0..2 and
+ * Lz-3..Lz-1).  thermal = 0 (the default): adiabatic no-slip half-way bounce-back.
+ * thermal = 1: isothermal walls at T_bottom (z = -1/2) and T_top (z = Lz - 1/2): a
+ * population whose pull source row lies beyond a wall takes the value of one of three
+ * ghost rows holding f^eq(rho_w(x), 0, T_w) (the unshifted equilibrium at rest), with
+ * the ghost density of each column set so that the mass the step moves into the ghost
+ * rows of that column equals the mass the ghost rows send into the lattice (total mass
+ * is conserved).  With thermal walls, lbm_step_push, the slab decomposition, the
+ * ensembles and the adjoint return LBM_ESTATE (they implement the bounce-back rule
+ * only).  LBM_EINVAL for thermal outside {0, 1} or non-positive / non-finite wall
+ * temperatures.  Host only; takes effect from the next step.                          */
+int lbm_set_walls(lbm_ctx *c, int thermal, double T_bottom, double T_top);
+
 /* Push form of the step (Sec. III.B compares "push" and "pull"; lbm_step is the pull form,
  * whose stored state is post-collision, f <- C(P f)).  lbm_step_push advances a state
  * stored post-propagation (pre-collision), g <- P(C g): every site reads its own

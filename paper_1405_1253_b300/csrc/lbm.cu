@@ -22,6 +22,7 @@
 #include "init_diag.cuh"
 #include "adjoint.cuh"
 #include "adjoint_ff.cuh"
+#include "walls.cuh"
 #include "ensemble.cuh"
 
 using namespace lbm;
@@ -190,6 +191,9 @@ struct lbm_ctx {
     // host-buffer stepping (lbm_step_host): copy streams and their events, made on first use
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t e_in = nullptr, e_step = nullptr, e_out = nullptr;
+    // wall rule: 0 half-way bounce-back, 1 thermal walls (lbm_set_walls)
+    int thermal = 0;
+    ThermalWall tw{};
 };
 
 static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
@@ -242,6 +246,33 @@ static void launch_step(int prec, const void* fin, void* fout, const StepParams&
         default: launch_step_f32((const float*)fin, (float*)fout, p, t, st); break;
     }
 }
+
+// One step of context c from fin to fout with its wall rule (one launch either way).
+static void ctx_step(const lbm_ctx* c, const void* fin, void* fout, const StepParams& p, cudaStream_t st) {
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    if (!c->thermal) {
+        launch_step(c->prec, fin, fout, p, t, st);
+        return;
+    }
+    const int blocks = tiling_blocks(t);
+    switch (c->prec) {
+        case LBM_F64:
+            k_step_f64_thermal<<<blocks, BLOCK_Z, 0, st>>>((const double*)fin, (double*)fout, p, t, c->tw);
+            break;
+        case LBM_F64_FF:
+            k_step_ff_thermal<<<blocks, BLOCK_Z, 0, st>>>((const double*)fin, (double*)fout,
+                                                          ff_params(p, quad_w_shell()), t, c->tw);
+            break;
+        default:
+            k_step_f32_thermal<<<blocks, BLOCK_Z, 0, st>>>((const float*)fin, (float*)fout, f32_params(p), t, c->tw);
+            break;
+    }
+}
+
+#define NEED_BOUNCE_BACK(c, what)                                                               \
+    do {                                                                                        \
+        if ((c)->thermal) return fail(LBM_ESTATE, what " supports the bounce-back walls only"); \
+    } while (0)
 
 template <class S>
 static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renorm) {
@@ -420,14 +451,26 @@ int lbm_init_layers(lbm_ctx* c, const lbm_layers_desc* d) {
 // ---------------------------------------------------------------------------------
 // Step
 // ---------------------------------------------------------------------------------
+int lbm_set_walls(lbm_ctx* c, int thermal, double T_bottom, double T_top) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (thermal != 0 && thermal != 1) return fail(LBM_EINVAL, "thermal must be 0 or 1");
+    if (thermal && !(T_bottom > 0.0 && T_top > 0.0 && std::isfinite(T_bottom) && std::isfinite(T_top)))
+        return fail(LBM_EINVAL, "wall temperatures must be positive and finite");
+    if (thermal) {
+        thermal_wall_q(quad_w_shell(), g_quad.r, T_bottom, 0, c->tw.q[0]);
+        thermal_wall_q(quad_w_shell(), g_quad.r, T_top, 1, c->tw.q[1]);
+    }
+    c->thermal = thermal;
+    return LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int nsteps) {
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
-    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     for (int s = 0; s < nsteps; s++) {
-        launch_step(c->prec, c->buf[c->cur], c->buf[c->cur ^ 1], p, t, c->stream);
+        ctx_step(c, c->buf[c->cur], c->buf[c->cur ^ 1], p, c->stream);
         LAUNCH_CHECK();
         c->cur ^= 1;
     }
@@ -437,6 +480,7 @@ int lbm_step(lbm_ctx* c, int nsteps) {
 int lbm_step_push(lbm_ctx* c, int nsteps) {
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    NEED_BOUNCE_BACK(c, "lbm_step_push");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
@@ -541,7 +585,6 @@ int lbm_step_host(lbm_ctx* c, const double* const* host_in, double* const* host_
     }
     const size_t bytes = (size_t)Q * c->Lx * c->Lz * sizeof(double);
     const StepParams p = step_params(c);
-    const Tiling tl = make_tiling(p.Lx, p.Lz, BLOCK_Z);
     void* X = c->buf[c->cur];         // the step's input, filled from the host
     void* Y = c->buf[c->cur ^ 1];     // the step's output, read back to the host
     // Step t: X <- host_in[t] (s_in), Y = step(X) (c's stream), host_out[t] <- Y (s_out).
@@ -556,7 +599,7 @@ int lbm_step_host(lbm_ctx* c, const double* const* host_in, double* const* host_
         CU(cudaEventRecord(c->e_in, c->s_in));
         CU(cudaStreamWaitEvent(c->stream, c->e_in, 0));
         CU(cudaStreamWaitEvent(c->stream, c->e_out, 0));
-        launch_step(c->prec, X, Y, p, tl, c->stream);
+        ctx_step(c, X, Y, p, c->stream);
         LAUNCH_CHECK();
         CU(cudaEventRecord(c->e_step, c->stream));
         CU(cudaStreamWaitEvent(c->s_out, c->e_step, 0));
@@ -736,6 +779,7 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
 int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
     if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
     if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
+    NEED_BOUNCE_BACK(c, "the adjoint step");
     if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
@@ -815,6 +859,7 @@ static int ens_layout(lbm_ensemble* e) {
     int tb = 0;
     for (int i = 0; i < e->n; i++) {
         lbm_ctx* c = e->ctx[i];
+        NEED_BOUNCE_BACK(c, "an ensemble");
         EnsLattice& L = e->h_lats[i];
         L.buf[0] = c->buf[0];
         L.buf[1] = c->buf[1];
@@ -903,6 +948,7 @@ int lbm_ensemble_create(lbm_ensemble** out, int n, lbm_ctx* const* ctxs) {
         if (b->device != a->device || b->prec != a->prec || b->tau != a->tau || b->grav != a->grav ||
             b->stream != a->stream)
             return fail(LBM_EINVAL, "context %d differs from context 0 in device, precision, tau, g or stream", i);
+        NEED_BOUNCE_BACK(b, "an ensemble");
     }
     if (ctxs[0]->prec != LBM_F64_FF && ctxs[0]->prec != LBM_F32)
         return fail(LBM_EINVAL, "ensembles take LBM_F64_FF or LBM_F32 contexts");
@@ -1216,6 +1262,7 @@ int lbm_slabs_create(lbm_slabs** out, lbm_ctx* c, int nslab) {
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    NEED_BOUNCE_BACK(c, "the slab decomposition");
     if (nslab < 1 || c->Lx % nslab) return fail(LBM_EINVAL, "Lx = %d is not a multiple of nslab = %d", c->Lx, nslab);
     if (c->Lx / nslab < HX) return fail(LBM_EINVAL, "slabs of %d columns: need at least %d", c->Lx / nslab, HX);
     DeviceGuard dg(c->device);
@@ -1262,6 +1309,7 @@ int lbm_slabs_step(lbm_slabs* s, int nsteps, int overlap) {
     if (!s) return fail(LBM_EINVAL, "slabs is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     lbm_ctx* c = s->c;
+    NEED_BOUNCE_BACK(c, "the slab decomposition");
     DeviceGuard dg(c->device);
     StepParams p = step_params(c);
     p.Lx = s->W;                      // the kernels address one slab buffer

@@ -43,6 +43,7 @@ _SIGS = {
     "lbm_init_layers": (_i, [_vp, ctypes.POINTER(LayersDesc)]),
     "lbm_step": (_i, [_vp, _i]),
     "lbm_step_push": (_i, [_vp, _i]),
+    "lbm_set_walls": (_i, [_vp, _i, _d, _d]),
     "lbm_step_host": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i]),
     "lbm_propagate": (_i, [_vp]),
     "lbm_current": (_vp, [_vp]),
@@ -206,6 +207,11 @@ class Lattice:
         ins = (_vp * n)(*[ptr(a) for a in host_in])
         outs = (_vp * n)(*[ptr(a) for a in host_out])
         _check(_lib.lbm_step_host(self.ctx, ins, outs, n))
+
+    def set_walls(self, thermal: bool, T_bottom: float = 1.0, T_top: float = 1.0):
+        """Wall rule of step(): half-way bounce-back (thermal=False, the default) or
+        isothermal walls at T_bottom / T_top (see lbm_set_walls)."""
+        _check(_lib.lbm_set_walls(self.ctx, int(bool(thermal)), float(T_bottom), float(T_top)))
 
     def step_push(self, n: int = 1):
         """Push-form steps of a post-propagation state (see lbm_step_push)."""

@@ -1,7 +1,7 @@
 """The bounds-checked build (liblbm_checked.so, every population load and store index-checked):
 a child process running every kernel path — pull and push steps in every precision on edge
 shapes, propagate, moments and row statistics, the slabs, the ensemble in both launch modes,
-the adjoint, host stepping — must meet no out-of-range index."""
+the adjoint, thermal walls, host stepping — must meet no out-of-range index."""
 import os
 import subprocess
 import sys
@@ -59,6 +59,12 @@ def exercise():
         lam = torch.rand_like(f)
         out = torch.empty_like(f)
         A.adjoint_step(f, lam, out)
+    for prec in ("f64", "f64_ff", "f32"):
+        for Lx, Lz in ((23, 40), (2, 6)):
+            T = lbm.Lattice(Lx, Lz, 0.8, 1e-4, prec=prec)
+            T.init_from(W.Lattice(Lx, Lz, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=24))
+            T.set_walls(True, 1.05, 0.95)
+            T.step(2)
     H = lbm.Lattice(16, 48, 0.8, 1e-4, prec="f64_ff")
     a = np.ones(37 * 16 * 48)
     b = np.empty_like(a)
