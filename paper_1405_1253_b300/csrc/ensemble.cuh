@@ -49,28 +49,27 @@ __device__ __forceinline__ int ens_find(const EnsLattice* __restrict__ lats, int
     return lo;
 }
 
-// Physics shared by all lattices; per-lattice sizes are filled in per tile.
-template <class P>
-__device__ __forceinline__ P with_shape(P q, const EnsLattice& L) {
-    q.Lx = L.Lx;
-    q.Lz = L.Lz;
-    q.plane = L.plane;
-    return q;
-}
-
-// One tile of one lattice at step s of the launch (buffers chosen by parity).
+// One tile of one lattice at step s of the launch.  The buffers are chosen by parity with a
+// select, not an index into L.buf (a run-time index would put the struct in local memory);
+// the physics comes from the launch's parameter block, the shape from the lattice.
 template <class LD>
 __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, const StepParamsFF& qf,
                                         int* sbase) {
-    const double* fin = (const double*)L.buf[(L.cur + s) & 1];
-    double* fout = (double*)L.buf[(L.cur + s + 1) & 1];
-    tile_ff<LD>(fin, fout, with_shape(qf, L), L.t, local, sbase);
+    const bool odd = (L.cur + s) & 1;
+    const double* fin = (const double*)(odd ? L.buf[1] : L.buf[0]);
+    double* fout = (double*)(odd ? L.buf[0] : L.buf[1]);
+    tile_ff<LD>(fin, fout, qf, Shape{L.Lx, L.Lz, L.plane}, L.t, local, sbase);
 }
 template <class LD>
 __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, const StepParamsF& qs, int*) {
-    const float* fin = (const float*)L.buf[(L.cur + s) & 1];
-    float* fout = (float*)L.buf[(L.cur + s + 1) & 1];
-    tile_f32<LD>(fin, fout, with_shape(qs, L), L.t, local);
+    const bool odd = (L.cur + s) & 1;
+    const float* fin = (const float*)(odd ? L.buf[1] : L.buf[0]);
+    float* fout = (float*)(odd ? L.buf[0] : L.buf[1]);
+    StepParamsF q = qs;              // no arrays: stays in registers
+    q.Lx = L.Lx;
+    q.Lz = L.Lz;
+    q.plane = L.plane;
+    tile_f32<LD>(fin, fout, q, L.t, local);
 }
 
 // Resident blocks per SM requested from the compiler for a tile height of TZ threads

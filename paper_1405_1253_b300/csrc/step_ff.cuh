@@ -243,22 +243,34 @@ __device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const St
     collide_ff(moments_ff(src), src, dst, p);
 }
 
+// Lattice shape of one tile's lattice, apart from the physics in StepParamsFF (the ensemble
+// runs lattices of several shapes under one parameter block; copying that block to change
+// its shape would put its per-shell constants, indexed at run time, into local memory).
+struct Shape {
+    int Lx, Lz, plane;
+};
+
 // One tile b of the lattice tiling t, pulled from global memory; sbase: Q ints of shared
 // memory.  All threads of the block must call this (it synchronises once after filling sbase).
 template <class LD>
 __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
-                                       const StepParamsFF& p, Tiling t, int b, int* sbase) {
+                                       const StepParamsFF& p, Shape sh, Tiling t, int b, int* sbase) {
     const bool wall_tile = tile_is_wall(t, b);
     if (!wall_tile) {
-        fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+        fill_pull_bases(sbase, tile_column(t, b), sh.Lx, sh.Lz, sh.plane);
         __syncthreads();
     }
     SiteAddr ad;
     bool wall;
-    if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    const DstSite dst{fout, ad.dst(), p.plane};
+    if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
+    const DstSite dst{fout, ad.dst(), sh.plane};
     if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, dst, p);
     else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, dst, p);
+}
+template <class LD>
+__device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
+                                       const StepParamsFF& p, Tiling t, int b, int* sbase) {
+    tile_ff<LD>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, b, sbase);
 }
 
 // Push form of one tile: aligned reads of the site's own populations, results written
