@@ -132,6 +132,13 @@ int lbm_step_push(lbm_ctx *c, int nsteps);
  * steps from f.  Asynchronous.                                                        */
 int lbm_propagate(lbm_ctx *c);
 
+/* Steps through caller-owned device buffers: states[j + 1] = step(states[j]) for
+ * j = 0 .. n - 2 (n >= 0 pointers, each 37*Lx*Lz populations in the context's storage
+ * precision and layout), with the context's tau, g and wall rule; the context's own
+ * state is neither read nor changed.  Consecutive buffers must differ.  Serves the
+ * recomputation of a checkpoint segment before its adjoint without copies.  Asynchronous. */
+int lbm_step_chain(lbm_ctx *c, void *const *states, int n);
+
 /* Device address of the buffer holding the current state (buf0 or buf1); NULL for a
  * NULL context.                                                                       */
 void *lbm_current(lbm_ctx *c);
@@ -205,6 +212,14 @@ int lbm_global_sums(lbm_ctx *c, double out[2]);
  * agree with the native form to ~1e-15 of the site's largest |lam_next|).  Both assume
  * |u| well below 0.3 and finite inputs.  Asynchronous.                                */
 int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, double *lam_out);
+
+/* n adjoint steps in one call: with lam_a holding lam_n on entry, applies lbm_adjoint_step
+ * for t = n - 1 down to 0 with f_t = states[t], ping-ponging between lam_a and lam_b;
+ * *out_index = 0 if lam_0 ends in lam_a, 1 if in lam_b.  The states (device, FP64 layout)
+ * must not alias lam_a or lam_b.  Same precision and wall conditions as lbm_adjoint_step.
+ * Asynchronous.                                                                         */
+int lbm_adjoint_chain(lbm_ctx *c, const double *const *states, int n, double *lam_a, double *lam_b,
+                      int *out_index);
 
 /* Adjoint of the width readout (FP64 storage): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
  * with dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device, FP64 layout).

@@ -4,12 +4,13 @@ The loss is L = L_u + L_d, the threshold widths of the two fronts (Sec. IV) at s
 the three-layer run started from the perturbed initial state (Sec. I).  The forward pass
 runs N fused steps, keeping every K-th state as a device checkpoint.  The backward pass
 starts from lam_N = dL/df_N (width adjoint -> mean profile -> T -> f), then, segment by
-segment from the last, recomputes the K states of the segment from its checkpoint into a
-device buffer and applies the adjoint step K times (lam_t = P^T J_C^T lam_{t+1}); the
+segment from the last, recomputes the K states of the segment from its checkpoint into
+device buffers (lbm_step_chain) and applies the adjoint step K times (lbm_adjoint_chain,
+lam_t = P^T J_C^T lam_{t+1}); the
 adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA library;
 this module only orders the calls and owns the buffers (through PyTorch).
 
-Memory: (N/K) checkpoints + K segment states + 2 adjoint fields, each 37 Lx Lz doubles.
+Memory: (N/K) checkpoints + (K - 1) segment states + 2 adjoint fields, each 37 Lx Lz doubles.
 """
 from __future__ import annotations
 
@@ -55,9 +56,10 @@ class WidthGradient:
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
         self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]
-        self.seg = torch.empty((self.K, n), dtype=torch.float64, device=dev)
+        # states f_{sK+1} .. f_{sK+K-1} of a segment (f_{sK} is its checkpoint)
+        self.seg = torch.empty((self.K - 1, n), dtype=torch.float64, device=dev)
         self.lam = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
-        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=8 * n * self.K,
+        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=8 * n * (self.K - 1),
                                   state_bytes=8 * n)
         self._amps = None
 
@@ -98,15 +100,12 @@ class WidthGradient:
         cur, nxt = self.lam
         self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
         for s in range(self.N // self.K - 1, -1, -1):
-            # recompute the K states f_{sK} .. f_{sK+K-1} of this segment
-            self.L.set_populations(self.ckpts[s])
-            for j in range(self.K):
-                self.L.populations_device(self.seg[j])
-                if j + 1 < self.K:
-                    self.L.step(1)
+            # recompute f_{sK+1} .. f_{sK+K-1} from the checkpoint into the segment buffers
+            # (one library call), then the K adjoint steps of the segment (one call)
+            states = [self.ckpts[s]] + [self.seg[j] for j in range(self.K - 1)]
+            self.L.step_chain(states)
             self.stats.recompute_steps += self.K - 1
-            for j in range(self.K - 1, -1, -1):
-                self.L.adjoint_step(self.seg[j], cur, nxt)
+            if self.L.adjoint_chain(states, cur, nxt) == 1:
                 cur, nxt = nxt, cur
             self.stats.adjoint_steps += self.K
         amp_lo, amp_hi = self._amps

@@ -500,6 +500,22 @@ int lbm_step_push(lbm_ctx* c, int nsteps) {
     return LBM_OK;
 }
 
+int lbm_step_chain(lbm_ctx* c, void* const* states, int n) {
+    if (!c || !states) return fail(LBM_EINVAL, "NULL argument");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    for (int j = 0; j < n; j++) {
+        if (!states[j]) return fail(LBM_EINVAL, "state %d is NULL", j);
+        if (j > 0 && states[j] == states[j - 1]) return fail(LBM_EINVAL, "states %d and %d are the same buffer", j - 1, j);
+    }
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    for (int j = 0; j + 1 < n; j++) {
+        ctx_step(c, states[j], states[j + 1], p, c->stream);
+        LAUNCH_CHECK();
+    }
+    return LBM_OK;
+}
+
 int lbm_propagate(lbm_ctx* c) {
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     DeviceGuard dg(c->device);
@@ -776,13 +792,8 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
 // ---------------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------------
-int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
-    if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
-    NEED_BOUNCE_BACK(c, "the adjoint step");
-    if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
-    DeviceGuard dg(c->device);
-    const StepParams p = step_params(c);
+static void launch_adjoint(const lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out,
+                           const StepParams& p) {
     if (c->prec == LBM_F64_FF) {
         launch_adjoint_ff(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z),
                           c->stream);
@@ -790,7 +801,39 @@ int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, doub
         dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
         k_adjoint_f64<<<grid, BLOCK_Z, 0, c->stream>>>(f_t, lam_next, lam_out, p);
     }
+}
+
+int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
+    if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
+    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
+    NEED_BOUNCE_BACK(c, "the adjoint step");
+    if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
+    DeviceGuard dg(c->device);
+    launch_adjoint(c, f_t, lam_next, lam_out, step_params(c));
     LAUNCH_CHECK();
+    return LBM_OK;
+}
+
+int lbm_adjoint_chain(lbm_ctx* c, const double* const* states, int n, double* lam_a, double* lam_b, int* out_index) {
+    if (!c || !states || !lam_a || !lam_b || !out_index) return fail(LBM_EINVAL, "NULL argument");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
+    NEED_BOUNCE_BACK(c, "the adjoint step");
+    if (lam_a == lam_b) return fail(LBM_EINVAL, "lam_a and lam_b must differ");
+    for (int j = 0; j < n; j++) {
+        if (!states[j]) return fail(LBM_EINVAL, "state %d is NULL", j);
+        if (states[j] == lam_a || states[j] == lam_b) return fail(LBM_EINVAL, "state %d aliases an adjoint buffer", j);
+    }
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    double* lam[2] = {lam_a, lam_b};
+    int cur = 0;
+    for (int j = n - 1; j >= 0; j--) {
+        launch_adjoint(c, states[j], lam[cur], lam[cur ^ 1], p);
+        LAUNCH_CHECK();
+        cur ^= 1;
+    }
+    *out_index = cur;
     return LBM_OK;
 }
 

@@ -44,6 +44,8 @@ _SIGS = {
     "lbm_step": (_i, [_vp, _i]),
     "lbm_step_push": (_i, [_vp, _i]),
     "lbm_set_walls": (_i, [_vp, _i, _d, _d]),
+    "lbm_step_chain": (_i, [_vp, _vp, _i]),
+    "lbm_adjoint_chain": (_i, [_vp, _vp, _i, _vp, _vp, ctypes.POINTER(_i)]),
     "lbm_step_host": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i]),
     "lbm_propagate": (_i, [_vp]),
     "lbm_current": (_vp, [_vp]),
@@ -285,6 +287,20 @@ class Lattice:
         return out
 
     # -- adjoint (FP64 contexts) -------------------------------------------------------
+    def step_chain(self, states):
+        """states[j + 1] = step(states[j]) through the given device tensors (lbm_step_chain)."""
+        ptrs = (_vp * len(states))(*[t.data_ptr() for t in states])
+        _check(_lib.lbm_step_chain(self.ctx, ptrs, len(states)))
+
+    def adjoint_chain(self, states, lam_a, lam_b) -> int:
+        """len(states) adjoint steps from lam_a (lam_n) back to lam_0; returns 0 or 1, the
+        index of the tensor (lam_a, lam_b) that holds lam_0 (lbm_adjoint_chain)."""
+        ptrs = (_vp * len(states))(*[t.data_ptr() for t in states])
+        idx = _i(0)
+        _check(_lib.lbm_adjoint_chain(self.ctx, ptrs, len(states), lam_a.data_ptr(), lam_b.data_ptr(),
+                                      ctypes.byref(idx)))
+        return idx.value
+
     def adjoint_step(self, f_t, lam_next, lam_out):
         _check(_lib.lbm_adjoint_step(self.ctx, f_t.data_ptr(), lam_next.data_ptr(), lam_out.data_ptr()))
 

@@ -156,3 +156,30 @@ def test_ff_adjoint_matches_native_ragged(env, Lx, Lz):
     a = adjoint_of(torch, lbm, lat, "f64_ff", f, lam)
     b = adjoint_of(torch, lbm, lat, "f64", f, lam)
     assert float((a - b).abs().max() / b.abs().max()) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64_ff"])
+def test_step_and_adjoint_chains_equal_single_calls(env, prec):
+    """lbm_step_chain through caller buffers equals lbm_step, and lbm_adjoint_chain equals
+    repeated lbm_adjoint_step (bit for bit: the same kernels on the same inputs)."""
+    torch, lbm = env
+    lat = W.Lattice(24, 70, tau=0.75, grav=2e-4, K=3, sigma=1.0, seed=12)
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
+    L.init_from(lat)
+    f0 = L.populations_device().clone()
+    states = [f0] + [torch.empty_like(f0) for _ in range(4)]
+    L.step_chain(states)
+    for j in range(1, 5):
+        L.step(1)
+        assert torch.equal(states[j], L.populations_device())
+    lam = torch.from_numpy(np.random.default_rng(13).standard_normal(f0.numel())).cuda()
+    a, b = lam.clone(), torch.empty_like(lam)
+    idx = L.adjoint_chain(states, a, b)
+    ref, tmp = lam.clone(), torch.empty_like(lam)
+    for j in range(4, -1, -1):
+        L.adjoint_step(states[j], ref, tmp)
+        ref, tmp = tmp, ref
+    assert idx == 1 and torch.equal((a, b)[idx], ref)
+    with pytest.raises(lbm.LBMError):
+        L.adjoint_chain([states[0], a], a, b)            # a state aliasing an adjoint buffer
+    L.close()
