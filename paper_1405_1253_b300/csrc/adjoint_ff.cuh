@@ -295,7 +295,8 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
         adjoint_site_ff(SrcGlobal<false, LoadNC>{ft, ad, sbase}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
 }
 
-__global__ void __launch_bounds__(BLOCK_Z, 4)
+// 5 resident blocks per SM (96 registers, 20 warps): 4.6% faster than 4 blocks (114 registers)
+__global__ void __launch_bounds__(BLOCK_Z, 5)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
              AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
