@@ -41,7 +41,7 @@ struct AdjParamsFF {
 
 // a * c, not renormalised.
 __device__ __forceinline__ ff ff_mul_c3_u(ff a, const ff3& c) {
-    const float p = a.hi * c.hi;
+    const float p = __fmul_rn(a.hi, c.hi);
     float e = fmaf(a.hi, c.hi, -p);
     e = fmaf(a.hi, c.lo2, e);
     e = fmaf(a.hi, c.lo, e);
@@ -295,12 +295,39 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
         adjoint_site_ff(SrcGlobal<false, LoadNC>{ft, ad, sbase}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
 }
 
-// 5 resident blocks per SM (96 registers, 20 warps): 4.6% faster than 4 blocks (114 registers)
-__global__ void __launch_bounds__(BLOCK_Z, 5)
+// Two register budgets: 5 resident blocks per SM (96 registers, 20 warps; 4.6% faster than 4
+// blocks with 114 registers on large lattices) and 7 (72 registers, a small spill; 4% more time
+// per block, but one wave where the 5-block form needs two, as on 256 x 512).
+template <int MINB>
+__global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
              AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
     adjoint_tile_ff(ft, lam_next, lam_out, p, t, blockIdx.x, sbase);
+}
+
+// Relative time per block of the 7-block form (measured on 1024 x 2048: 0.647 vs 0.623 ms).
+constexpr double ADJ_FF_COST7 = 1.04;
+
+// Whether the 7-block form is expected to finish first: blocks rounded up to whole waves of
+// each form's resident slots, weighted by the time per block.
+inline bool adjoint_ff_use7(int blocks) {
+    static int s5 = 0, s7 = 0, dev = -1;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev) {
+        int sms = 0, b5 = 0, b7 = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, k_adjoint_ff<5>, BLOCK_Z, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b7, k_adjoint_ff<7>, BLOCK_Z, 0);
+        s5 = sms * b5;
+        s7 = sms * b7;
+        dev = d;
+    }
+    if (s5 <= 0 || s7 <= 0) return false;
+    const double padded5 = (double)((blocks + s5 - 1) / s5) * s5;
+    const double padded7 = (double)((blocks + s7 - 1) / s7) * s7;
+    return padded7 * ADJ_FF_COST7 < padded5;
 }
 
 // w_shell: the shell weights; r: the lattice constant (both binary64).
@@ -327,7 +354,9 @@ inline AdjParamsFF adj_ff_params(const StepParams& p, const double* w_shell, dou
 inline void launch_adjoint_ff(const double* ft, const double* lam_next, double* lam_out, const StepParams& p,
                               const double* w_shell, double r, const Tiling& t, cudaStream_t st) {
     const AdjParamsFF q = adj_ff_params(p, w_shell, r);
-    k_adjoint_ff<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+    const int blocks = tiling_blocks(t);
+    if (adjoint_ff_use7(blocks)) k_adjoint_ff<7><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+    else k_adjoint_ff<5><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
 }
 
 }  // namespace lbm

@@ -9,6 +9,11 @@
 // below skip the final renormalisation: their result keeps |lo| a few units of 2^-24
 // below |hi|, which every consumer here tolerates; their error is a few units of 2^-48
 // relative to the operands.
+//
+// The leading products are written __fmul_rn: the compiler may not contract them into a
+// following add (an FMA there would round the sum of the exact product instead of the sum of
+// the rounded one the error terms describe), so the transformations stay exact and the
+// results do not depend on how a kernel's registers and schedule come out.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -56,7 +61,7 @@ __device__ __forceinline__ ff ff_add_big_u(ff a, ff b) {
 
 // Product, not renormalised.
 __device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
@@ -69,7 +74,7 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 
 // Product with an FP32 number (exact small integers in particular), not renormalised.
 __device__ __forceinline__ ff ff_mul_f_u(ff a, float b) {
-    const float p = a.hi * b;
+    const float p = __fmul_rn(a.hi, b);
     float e = fmaf(a.hi, b, -p);
     e = fmaf(a.lo, b, e);
     return ff{p, e};
@@ -94,7 +99,7 @@ __device__ __forceinline__ ff3 ff3_of(const float (&t)[3]) { return ff3{t[0], t[
 
 // a * c, renormalised (the a.lo * c.lo term, ~2^-48 relative, is dropped as in ff_mul).
 __device__ __forceinline__ ff ff_mul_c3(ff a, const ff3& c) {
-    const float p = a.hi * c.hi;
+    const float p = __fmul_rn(a.hi, c.hi);
     float e = fmaf(a.hi, c.hi, -p);
     e = fmaf(a.hi, c.lo2, e);
     e = fmaf(a.hi, c.lo, e);
@@ -114,7 +119,7 @@ __device__ __forceinline__ ff ff_rcp(ff a) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.hi));
     float e = fmaf(-a.hi, y, 1.0f);
     e = fmaf(-a.lo, y, e);
-    return fast_two_sum(y, y * fmaf(e, e, e));
+    return fast_two_sum(y, __fmul_rn(y, fmaf(e, e, e)));
 }
 
 // ---------------------------------------------------------------------------------
