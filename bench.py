@@ -254,25 +254,28 @@ def bench_ensemble(torch, lbm, prec, steps, stream):
 
 
 def bench_adjoint(torch):
-    """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and
-    backward (recompute + adjoint) wall times and device memory."""
+    """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and backward
+    (recompute + adjoint) wall times and device memory, for both backward stores of the
+    float-float driver (moment records, segment states)."""
     from paper_1405_1253_b300 import adjoint
     lat = W.GRADIENT_256x512
-    drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT)
+    out = {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (f64_ff)"}
     m = lat.modes()
-    drv.forward(m.amp_lo, m.amp_hi)      # warm
-    drv.backward()
-    drv.forward(m.amp_lo, m.amp_hi)
-    g_lo, g_hi = drv.backward()
-    st = drv.stats
-    drv.close()
-    return {"workload": f"256x512, 2000 steps, checkpoint every 100, 16 modes per front ({drv.prec})",
-            "forward_s": st.forward_s, "backward_s": st.backward_s, "backward_over_forward": st.backward_s / st.forward_s,
-            "memory_bytes": st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes,
-            "forward_memory_bytes": 2 * st.state_bytes,
-            "memory_over_forward": (st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes) / (2 * st.state_bytes),
-            "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
-
+    for store in ("moments", "states"):
+        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, store=store)
+        drv.forward(m.amp_lo, m.amp_hi)      # warm
+        drv.backward()
+        drv.forward(m.amp_lo, m.amp_hi)
+        g_lo, g_hi = drv.backward()
+        st = drv.stats
+        drv.close()
+        mem = st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes
+        out[store] = {"forward_s": st.forward_s, "backward_s": st.backward_s,
+                      "backward_over_forward": st.backward_s / st.forward_s,
+                      "memory_bytes": mem, "forward_memory_bytes": 2 * st.state_bytes,
+                      "memory_over_forward": mem / (2 * st.state_bytes),
+                      "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
+    return out
 
 def bench_slabs(torch, lbm, lat, steps, stream, prec="f64_ff"):
     """The x-slab decomposition of Sec. III.B on this device (halos exchanged by device
@@ -345,9 +348,26 @@ def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        L.close()
         gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
         out[prec] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+        if prec == "f64_ff":
+            # the same adjoint with f_t given by its moment record: 32 + 296 + 296 = 624 B/site
+            wa, wb = torch.empty_like(f), torch.empty_like(f)
+            mom = [torch.empty(4 * lat.sites, dtype=torch.int64, device=f.device)]
+            L.record_moments(f, wa, wb, mom)
+            for i in range(3):
+                L.adjoint_chain_moments(mom, lam[i & 1], lam[(i + 1) & 1])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(steps):
+                L.adjoint_chain_moments(mom, lam[i & 1], lam[(i + 1) & 1])
+            e1.record(stream)
+            e1.synchronize()
+            msm = e0.elapsed_time(e1) / steps
+            gbm = 624 * lat.sites / (msm * 1e-3) / 1e9
+            out["f64_ff_moments"] = {"ms": msm, "mlups": lat.sites / (msm * 1e-3) / 1e6, "gbs": gbm,
+                                     "hbm_frac": gbm / peak, "bytes_per_site": 624}
+        L.close()
     out["f64_ff"]["traffic"] = ncu_traffic("k_adjoint_ff", lat.sites)
     return out
 

@@ -35,6 +35,7 @@
 #define LBM_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -220,6 +221,21 @@ int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, doub
  * Asynchronous.                                                                         */
 int lbm_adjoint_chain(lbm_ctx *c, const double *const *states, int n, double *lam_a, double *lam_b,
                       int *out_index);
+
+/* The adjoint of a step needs f_t only through the fixed-point moments (rho, J = sum c g,
+ * E = sum |c|^2 g, unit 2^-60, int64) of the pulled g = P f_t at each site, which the step
+ * itself forms.  lbm_record_moments runs n steps from f0 (device, FP64 layout, unchanged),
+ * alternating the outputs between work_a and work_b (the state after step j is in work_a for
+ * even j, work_b for odd j), and writes the moments of step j to moments[j]: 4*Lx*Lz int64,
+ * planes R, Jx, Jz, E of Lx*Lz sites each (site x*Lz + z).  lbm_adjoint_chain_moments is
+ * lbm_adjoint_chain with f_t replaced by such records (moments[t] for step t), bit for bit
+ * the same result, reading 32 instead of 296 bytes of f_t per site.  LBM_F64_FF contexts
+ * with bounce-back walls only (LBM_ESTATE otherwise); f0, work_a, work_b distinct.
+ * Asynchronous.                                                                         */
+int lbm_record_moments(lbm_ctx *c, const double *f0, int n, double *work_a, double *work_b,
+                       int64_t *const *moments);
+int lbm_adjoint_chain_moments(lbm_ctx *c, const int64_t *const *moments, int n, double *lam_a,
+                              double *lam_b, int *out_index);
 
 /* Adjoint of the width readout (FP64 storage): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
  * with dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device, FP64 layout).

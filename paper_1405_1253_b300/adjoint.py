@@ -10,7 +10,8 @@ lam_t = P^T J_C^T lam_{t+1}); the
 adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA library;
 this module only orders the calls and owns the buffers (through PyTorch).
 
-Memory: (N/K) checkpoints + (K - 1) segment states + 2 adjoint fields, each 37 Lx Lz doubles.
+Memory: (N/K) checkpoints and 2 adjoint fields, each 37 Lx Lz doubles, and per segment either
+(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through.
 """
 from __future__ import annotations
 
@@ -39,9 +40,12 @@ class AdjointStats:
 
 class WidthGradient:
     """Forward/backward driver for one lattice description on an FP64-storage context:
-    prec "f64_ff" (float-float step and adjoint, the default) or "f64" (native FP64)."""
+    prec "f64_ff" (float-float step and adjoint, the default) or "f64" (native FP64).
+    store "moments" (f64_ff only, its default): the backward recomputes each segment keeping
+    only the per-site moments the adjoint needs (32 bytes per site and step); "states": it
+    keeps the segment's states (296 bytes per site and step)."""
 
-    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff"):
+    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None):
         import torch
         if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
             raise ValueError("nsteps must be a positive multiple of ckpt")
@@ -52,14 +56,24 @@ class WidthGradient:
         if prec not in ("f64", "f64_ff"):
             raise ValueError("the adjoint needs FP64 storage (prec 'f64' or 'f64_ff')")
         self.prec = prec
+        self.store = store or ("moments" if prec == "f64_ff" else "states")
+        if self.store not in ("moments", "states") or (self.store == "moments" and prec != "f64_ff"):
+            raise ValueError("store is 'states', or 'moments' with prec 'f64_ff'")
         self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
         self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]
-        # states f_{sK+1} .. f_{sK+K-1} of a segment (f_{sK} is its checkpoint)
-        self.seg = torch.empty((self.K - 1, n), dtype=torch.float64, device=dev)
+        if self.store == "states":
+            # states f_{sK+1} .. f_{sK+K-1} of a segment (f_{sK} is its checkpoint)
+            self.seg = torch.empty((self.K - 1, n), dtype=torch.float64, device=dev)
+            seg_bytes = 8 * n * (self.K - 1)
+        else:
+            # moments of the K steps of a segment, and two states to step through
+            self.moms = torch.empty((self.K, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
+            self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+            seg_bytes = self.moms.numel() * 8 + 2 * 8 * n
         self.lam = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
-        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=8 * n * (self.K - 1),
+        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=seg_bytes,
                                   state_bytes=8 * n)
         self._amps = None
 
@@ -100,12 +114,20 @@ class WidthGradient:
         cur, nxt = self.lam
         self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
         for s in range(self.N // self.K - 1, -1, -1):
-            # recompute f_{sK+1} .. f_{sK+K-1} from the checkpoint into the segment buffers
-            # (one library call), then the K adjoint steps of the segment (one call)
-            states = [self.ckpts[s]] + [self.seg[j] for j in range(self.K - 1)]
-            self.L.step_chain(states)
-            self.stats.recompute_steps += self.K - 1
-            if self.L.adjoint_chain(states, cur, nxt) == 1:
+            if self.store == "states":
+                # recompute f_{sK+1} .. f_{sK+K-1} from the checkpoint into the segment buffers
+                # (one library call), then the K adjoint steps of the segment (one call)
+                states = [self.ckpts[s]] + [self.seg[j] for j in range(self.K - 1)]
+                self.L.step_chain(states)
+                self.stats.recompute_steps += self.K - 1
+                flip = self.L.adjoint_chain(states, cur, nxt)
+            else:
+                # recompute the K steps of the segment keeping only their moments
+                moms = [self.moms[j] for j in range(self.K)]
+                self.L.record_moments(self.ckpts[s], self.work[0], self.work[1], moms)
+                self.stats.recompute_steps += self.K
+                flip = self.L.adjoint_chain_moments(moms, cur, nxt)
+            if flip == 1:
                 cur, nxt = nxt, cur
             self.stats.adjoint_steps += self.K
         amp_lo, amp_hi = self._amps

@@ -141,11 +141,28 @@ struct AdjSums {
     ff A, Bx, Bz, U, C;
 };
 
-template <class FSRC, class DST>
-__device__ __forceinline__ void adjoint_site_ff(const FSRC& fsrc, const LamOwn& lsrc, const DST& dst,
+// The moments of the pulled f_t at the site: gathered and summed (as the step does), or read
+// from the record of the forward step (k_step_ff_moments); both give the same int64 sums.
+template <class FSRC>
+struct MomGather {
+    const FSRC& src;
+    __device__ __forceinline__ MomentsFix get() const { return moments_ff(src); }
+};
+struct MomStored {
+    const int64_t* __restrict__ m;
+    int plane, o;
+    __device__ __forceinline__ MomentsFix get() const {
+        const long long* q = (const long long*)m;
+        return MomentsFix{__ldg(q + LBM_IDX(o, 4 * plane)), __ldg(q + LBM_IDX(plane + o, 4 * plane)),
+                          __ldg(q + LBM_IDX(2 * plane + o, 4 * plane)), __ldg(q + LBM_IDX(3 * plane + o, 4 * plane))};
+    }
+};
+
+template <class MSRC, class DST>
+__device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& lsrc, const DST& dst,
                                                 const AdjParamsFF& p) {
     // -- pass 1: moments of the pulled f_t; block exponent of lam_{t+1} -----------------
-    const MomentsFix m = moments_ff(fsrc);
+    const MomentsFix m = msrc.get();
     uint32_t eb = 75u << 20;      // floor: zero and subnormal lam stay 0 after scaling
     static_for<Q>([&](auto l) { eb = max(eb, lsrc.template hiword<decltype(l)::value>() & 0x7FF00000u); });
     const int32_t S = (int32_t)eb - (int32_t)(1023u << 20);                  // (E_block - 1023) << 20
@@ -276,10 +293,11 @@ __device__ __forceinline__ void adjoint_site_ff(const FSRC& fsrc, const LamOwn& 
     }
 }
 
-// One tile b of the tiling t (the step's tiling: wall tiles, then interior columns).
-__device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const double* __restrict__ lam_next,
-                                                double* __restrict__ lam_out, const AdjParamsFF& p, Tiling t,
-                                                int b, int* sbase) {
+// One tile b of the tiling t (the step's tiling: wall tiles, then interior columns); the
+// moments come from f_t (ft) or, if ft is null, from the record mom.
+__device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const int64_t* __restrict__ mom,
+                                                const double* __restrict__ lam_next, double* __restrict__ lam_out,
+                                                const AdjParamsFF& p, Tiling t, int b, int* sbase) {
     const bool wall_tile = tile_is_wall(t, b);
     if (!wall_tile) {
         fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
@@ -289,10 +307,17 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
     bool wall;
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
     const LamOwn lsrc{lam_next, ad.dst(), p.plane};
-    if (wall)
-        adjoint_site_ff(SrcGlobal<true, LoadNC>{ft, ad, sbase}, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
-    else
-        adjoint_site_ff(SrcGlobal<false, LoadNC>{ft, ad, sbase}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
+    if (mom) {
+        const MomStored ms{mom, p.plane, ad.dst()};
+        if (wall) adjoint_site_ff(ms, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
+        else adjoint_site_ff(ms, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
+    } else if (wall) {
+        const SrcGlobal<true, LoadNC> src{ft, ad, sbase};
+        adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC>>{src}, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
+    } else {
+        const SrcGlobal<false, LoadNC> src{ft, ad, sbase};
+        adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
+    }
 }
 
 // Two register budgets: 5 resident blocks per SM (96 registers, 20 warps; 4.6% faster than 4
@@ -303,30 +328,44 @@ __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
              AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
-    adjoint_tile_ff(ft, lam_next, lam_out, p, t, blockIdx.x, sbase);
+    adjoint_tile_ff(ft, nullptr, lam_next, lam_out, p, t, blockIdx.x, sbase);
+}
+
+// The same adjoint with the moments of f_t read from the forward step's record.
+template <int MINB>
+__global__ void __launch_bounds__(BLOCK_Z, MINB)
+k_adjoint_ff_moments(const int64_t* __restrict__ mom, const double* __restrict__ lam_next,
+                     double* __restrict__ lam_out, AdjParamsFF p, Tiling t) {
+    __shared__ int sbase[Q];
+    adjoint_tile_ff(nullptr, mom, lam_next, lam_out, p, t, blockIdx.x, sbase);
 }
 
 // Relative time per block of the 7-block form (measured on 1024 x 2048: 0.647 vs 0.623 ms).
 constexpr double ADJ_FF_COST7 = 1.04;
 
+// Resident slots (SMs x blocks per SM) of the 5- and 7-block forms of one kernel, per device.
+struct TwoForms {
+    int s5 = 0, s7 = 0, dev = -1;
+};
+
 // Whether the 7-block form is expected to finish first: blocks rounded up to whole waves of
 // each form's resident slots, weighted by the time per block.
-inline bool adjoint_ff_use7(int blocks) {
-    static int s5 = 0, s7 = 0, dev = -1;
+template <class K5, class K7>
+inline bool pick_7_blocks(TwoForms& c, int blocks, K5 k5, K7 k7) {
     int d = 0;
     cudaGetDevice(&d);
-    if (d != dev) {
+    if (d != c.dev) {
         int sms = 0, b5 = 0, b7 = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, k_adjoint_ff<5>, BLOCK_Z, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b7, k_adjoint_ff<7>, BLOCK_Z, 0);
-        s5 = sms * b5;
-        s7 = sms * b7;
-        dev = d;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b5, k5, BLOCK_Z, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b7, k7, BLOCK_Z, 0);
+        c.s5 = sms * b5;
+        c.s7 = sms * b7;
+        c.dev = d;
     }
-    if (s5 <= 0 || s7 <= 0) return false;
-    const double padded5 = (double)((blocks + s5 - 1) / s5) * s5;
-    const double padded7 = (double)((blocks + s7 - 1) / s7) * s7;
+    if (c.s5 <= 0 || c.s7 <= 0) return false;
+    const double padded5 = (double)((blocks + c.s5 - 1) / c.s5) * c.s5;
+    const double padded7 = (double)((blocks + c.s7 - 1) / c.s7) * c.s7;
     return padded7 * ADJ_FF_COST7 < padded5;
 }
 
@@ -355,8 +394,23 @@ inline void launch_adjoint_ff(const double* ft, const double* lam_next, double* 
                               const double* w_shell, double r, const Tiling& t, cudaStream_t st) {
     const AdjParamsFF q = adj_ff_params(p, w_shell, r);
     const int blocks = tiling_blocks(t);
-    if (adjoint_ff_use7(blocks)) k_adjoint_ff<7><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
-    else k_adjoint_ff<5><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+    static TwoForms forms;
+    if (pick_7_blocks(forms, blocks, k_adjoint_ff<5>, k_adjoint_ff<7>))
+        k_adjoint_ff<7><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+    else
+        k_adjoint_ff<5><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+}
+
+inline void launch_adjoint_ff_moments(const int64_t* mom, const double* lam_next, double* lam_out,
+                                      const StepParams& p, const double* w_shell, double r, const Tiling& t,
+                                      cudaStream_t st) {
+    const AdjParamsFF q = adj_ff_params(p, w_shell, r);
+    const int blocks = tiling_blocks(t);
+    static TwoForms forms;
+    if (pick_7_blocks(forms, blocks, k_adjoint_ff_moments<5>, k_adjoint_ff_moments<7>))
+        k_adjoint_ff_moments<7><<<blocks, BLOCK_Z, 0, st>>>(mom, lam_next, lam_out, q, t);
+    else
+        k_adjoint_ff_moments<5><<<blocks, BLOCK_Z, 0, st>>>(mom, lam_next, lam_out, q, t);
 }
 
 }  // namespace lbm

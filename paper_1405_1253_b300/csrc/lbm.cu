@@ -837,6 +837,51 @@ int lbm_adjoint_chain(lbm_ctx* c, const double* const* states, int n, double* la
     return LBM_OK;
 }
 
+int lbm_record_moments(lbm_ctx* c, const double* f0, int n, double* work_a, double* work_b,
+                       int64_t* const* moments) {
+    if (!c || !f0 || !work_a || !work_b || !moments) return fail(LBM_EINVAL, "NULL argument");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    if (c->prec != LBM_F64_FF) return fail(LBM_ESTATE, "moment records need an LBM_F64_FF context");
+    NEED_BOUNCE_BACK(c, "the adjoint step");
+    if (work_a == work_b || f0 == work_a || f0 == work_b) return fail(LBM_EINVAL, "f0, work_a, work_b must differ");
+    for (int j = 0; j < n; j++)
+        if (!moments[j]) return fail(LBM_EINVAL, "moment record %d is NULL", j);
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    const StepParamsFF q = ff_params(p, quad_w_shell());
+    double* w[2] = {work_a, work_b};
+    for (int j = 0; j < n; j++) {
+        const double* fin = j == 0 ? f0 : w[(j - 1) & 1];
+        k_step_ff_moments<<<tiling_blocks(t), BLOCK_Z, 0, c->stream>>>(fin, w[j & 1], q, t, moments[j]);
+        LAUNCH_CHECK();
+    }
+    return LBM_OK;
+}
+
+int lbm_adjoint_chain_moments(lbm_ctx* c, const int64_t* const* moments, int n, double* lam_a, double* lam_b,
+                              int* out_index) {
+    if (!c || !moments || !lam_a || !lam_b || !out_index) return fail(LBM_EINVAL, "NULL argument");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    if (c->prec != LBM_F64_FF) return fail(LBM_ESTATE, "moment records need an LBM_F64_FF context");
+    NEED_BOUNCE_BACK(c, "the adjoint step");
+    if (lam_a == lam_b) return fail(LBM_EINVAL, "lam_a and lam_b must differ");
+    for (int j = 0; j < n; j++)
+        if (!moments[j]) return fail(LBM_EINVAL, "moment record %d is NULL", j);
+    DeviceGuard dg(c->device);
+    const StepParams p = step_params(c);
+    const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    double* lam[2] = {lam_a, lam_b};
+    int cur = 0;
+    for (int j = n - 1; j >= 0; j--) {
+        launch_adjoint_ff_moments(moments[j], lam[cur], lam[cur ^ 1], p, quad_w_shell(), g_quad.r, t, c->stream);
+        LAUNCH_CHECK();
+        cur ^= 1;
+    }
+    *out_index = cur;
+    return LBM_OK;
+}
+
 int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double* lam_out) {
     if (!c || !f || !dL_dTbar || !lam_out) return fail(LBM_EINVAL, "NULL argument");
     if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");

@@ -237,10 +237,30 @@ __device__ __forceinline__ void collide_ff(const MomentsFix& m, const SRC& src, 
     }
 }
 
-// The collide of one site: src gives its 37 populations g, dst takes the 37 results.
-template <class SRC, class DST>
-__device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p) {
-    collide_ff(moments_ff(src), src, dst, p);
+// Where a step leaves each site's fixed-point moments: nowhere (the step), or four planes of
+// int64 (R, Jx, Jz, E at site o; the adjoint of that step needs only these, not the state).
+struct NoMoments {
+    __device__ __forceinline__ void put(const MomentsFix&, int) const {}
+};
+struct MomentsOut {
+    int64_t* __restrict__ m;
+    int plane;
+    __device__ __forceinline__ void put(const MomentsFix& v, int o) const {
+        m[LBM_IDX(o, 4 * plane)] = v.R;
+        m[LBM_IDX(plane + o, 4 * plane)] = v.Jx;
+        m[LBM_IDX(2 * plane + o, 4 * plane)] = v.Jz;
+        m[LBM_IDX(3 * plane + o, 4 * plane)] = v.E;
+    }
+};
+
+// The collide of one site: src gives its 37 populations g, dst takes the 37 results; mo
+// records the moments of the site (index o).
+template <class SRC, class DST, class MOUT = NoMoments>
+__device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p,
+                                        const MOUT& mo = MOUT{}, int o = 0) {
+    const MomentsFix m = moments_ff(src);
+    mo.put(m, o);
+    collide_ff(m, src, dst, p);
 }
 
 // Lattice shape of one tile's lattice, apart from the physics in StepParamsFF (the ensemble
@@ -252,9 +272,10 @@ struct Shape {
 
 // One tile b of the lattice tiling t, pulled from global memory; sbase: Q ints of shared
 // memory.  All threads of the block must call this (it synchronises once after filling sbase).
-template <class LD>
+template <class LD, class MOUT = NoMoments>
 __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
-                                       const StepParamsFF& p, Shape sh, Tiling t, int b, int* sbase) {
+                                       const StepParamsFF& p, Shape sh, Tiling t, int b, int* sbase,
+                                       const MOUT& mo = MOUT{}) {
     const bool wall_tile = tile_is_wall(t, b);
     if (!wall_tile) {
         fill_pull_bases(sbase, tile_column(t, b), sh.Lx, sh.Lz, sh.plane);
@@ -264,8 +285,8 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
     bool wall;
     if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
     const DstSite dst{fout, ad.dst(), sh.plane};
-    if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, dst, p);
-    else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, dst, p);
+    if (wall) site_ff(SrcGlobal<true, LD>{fin, ad, sbase}, dst, p, mo, ad.dst());
+    else site_ff(SrcGlobal<false, LD>{fin, ad, sbase}, dst, p, mo, ad.dst());
 }
 template <class LD>
 __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
@@ -296,6 +317,14 @@ __global__ void __launch_bounds__(BLOCK_Z, 7)
 k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
     tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
+}
+
+// One step that also records every site's moments (for the adjoint of this step).
+__global__ void __launch_bounds__(BLOCK_Z, 7)
+k_step_ff_moments(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t,
+                  int64_t* __restrict__ mom) {
+    __shared__ int sbase[Q];
+    tile_ff<LoadNC>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase, MomentsOut{mom, p.plane});
 }
 
 inline ff ff_host(double v) {

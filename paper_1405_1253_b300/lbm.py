@@ -46,6 +46,8 @@ _SIGS = {
     "lbm_set_walls": (_i, [_vp, _i, _d, _d]),
     "lbm_step_chain": (_i, [_vp, _vp, _i]),
     "lbm_adjoint_chain": (_i, [_vp, _vp, _i, _vp, _vp, ctypes.POINTER(_i)]),
+    "lbm_record_moments": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "lbm_adjoint_chain_moments": (_i, [_vp, _vp, _i, _vp, _vp, ctypes.POINTER(_i)]),
     "lbm_step_host": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i]),
     "lbm_propagate": (_i, [_vp]),
     "lbm_current": (_vp, [_vp]),
@@ -299,6 +301,22 @@ class Lattice:
         idx = _i(0)
         _check(_lib.lbm_adjoint_chain(self.ctx, ptrs, len(states), lam_a.data_ptr(), lam_b.data_ptr(),
                                       ctypes.byref(idx)))
+        return idx.value
+
+    def record_moments(self, f0, work_a, work_b, moments):
+        """len(moments) steps from f0 through work_a / work_b, recording each step's moments
+        (int64 tensors of 4 Lx Lz) for the adjoint (lbm_record_moments)."""
+        ptrs = (_vp * len(moments))(*[t.data_ptr() for t in moments])
+        _check(_lib.lbm_record_moments(self.ctx, f0.data_ptr(), len(moments), work_a.data_ptr(), work_b.data_ptr(),
+                                       ptrs))
+
+    def adjoint_chain_moments(self, moments, lam_a, lam_b) -> int:
+        """adjoint_chain with f_t given by its moment records; returns the index of the
+        tensor (lam_a, lam_b) holding lam_0 (lbm_adjoint_chain_moments)."""
+        ptrs = (_vp * len(moments))(*[t.data_ptr() for t in moments])
+        idx = _i(0)
+        _check(_lib.lbm_adjoint_chain_moments(self.ctx, ptrs, len(moments), lam_a.data_ptr(), lam_b.data_ptr(),
+                                              ctypes.byref(idx)))
         return idx.value
 
     def adjoint_step(self, f_t, lam_next, lam_out):

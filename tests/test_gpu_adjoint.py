@@ -183,3 +183,31 @@ def test_step_and_adjoint_chains_equal_single_calls(env, prec):
     with pytest.raises(lbm.LBMError):
         L.adjoint_chain([states[0], a], a, b)            # a state aliasing an adjoint buffer
     L.close()
+
+
+def test_moment_records_give_the_same_adjoint(env):
+    """lbm_record_moments steps like lbm_step (bit for bit), and the adjoint from its moment
+    records equals the adjoint from the states (the same int64 moments enter the same code)."""
+    torch, lbm = env
+    lat = W.Lattice(20, 150, tau=0.7, grav=2e-4, K=3, sigma=1.0, seed=14)
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64_ff")
+    L.init_from(lat)
+    f0 = L.populations_device().clone()
+    states = [f0] + [torch.empty_like(f0) for _ in range(4)]
+    L.step_chain(states)
+    wa, wb = torch.empty_like(f0), torch.empty_like(f0)
+    moms = [torch.empty(4 * lat.Lx * lat.Lz, dtype=torch.int64, device=f0.device) for _ in range(5)]
+    L.record_moments(f0, wa, wb, moms)
+    torch.cuda.synchronize()
+    assert torch.equal(wb, states[4])               # after step 3 (odd: work_b)
+    lam = torch.from_numpy(np.random.default_rng(15).standard_normal(f0.numel())).cuda()
+    a1, b1 = lam.clone(), torch.empty_like(lam)
+    i1 = L.adjoint_chain(states, a1, b1)
+    a2, b2 = lam.clone(), torch.empty_like(lam)
+    i2 = L.adjoint_chain_moments(moms, a2, b2)
+    assert i1 == i2 and torch.equal((a1, b1)[i1], (a2, b2)[i2])
+    L.close()
+    F = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64")
+    with pytest.raises(lbm.LBMError) as e:
+        F.record_moments(f0, wa, wb, moms)
+    assert e.value.code == lbm.LBM_ESTATE

@@ -16,11 +16,11 @@ def adj():
     return adjoint
 
 
-@pytest.mark.parametrize("prec", ["f64", "f64_ff"])
-def test_gradient_matches_oracle_chain(adj, prec):
+@pytest.mark.parametrize("prec,store", [("f64", "states"), ("f64_ff", "states"), ("f64_ff", "moments")])
+def test_gradient_matches_oracle_chain(adj, prec, store):
     lat = W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=21)
     nsteps, ckpt = 6, 3
-    drv = adj.WidthGradient(lat, nsteps, ckpt, prec=prec)
+    drv = adj.WidthGradient(lat, nsteps, ckpt, prec=prec, store=store)
     m = lat.modes()
     Lval = drv.forward(m.amp_lo, m.amp_hi)
     g_lo, g_hi = drv.backward()
@@ -82,3 +82,16 @@ def test_gradient_vs_finite_differences_256x512_2000_steps(adj):
     per front, centred differences on every amplitude."""
     lat = W.GRADIENT_256x512
     fd_check(adj, lat, nsteps=W.GRADIENT_STEPS, ckpt=W.GRADIENT_CKPT)
+
+
+def test_moment_store_gives_the_same_gradient(adj):
+    """The two backward stores of the float-float driver give the same gradient bit for bit."""
+    lat = W.Lattice(40, 96, tau=0.8, grav=1e-4, K=3, sigma=1.0, seed=25)
+    m = lat.modes()
+    out = []
+    for store in ("states", "moments"):
+        drv = adj.WidthGradient(lat, 60, 20, store=store)
+        drv.forward(m.amp_lo, m.amp_hi)
+        out.append(np.concatenate(drv.backward()))
+        drv.close()
+    np.testing.assert_array_equal(out[0], out[1])
