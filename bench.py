@@ -52,6 +52,7 @@ KERNEL_SOURCES = {
     "k_step_f64": ("lattice.cuh", "common.cuh", "step_f64.cuh"),
     "k_step_f32": ("lattice.cuh", "common.cuh", "step_f32.cuh"),
     "k_adjoint_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
+    "k_adjoint_ff_moments": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
 }
 
 
@@ -366,7 +367,8 @@ def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
             msm = e0.elapsed_time(e1) / steps
             gbm = 624 * lat.sites / (msm * 1e-3) / 1e9
             out["f64_ff_moments"] = {"ms": msm, "mlups": lat.sites / (msm * 1e-3) / 1e6, "gbs": gbm,
-                                     "hbm_frac": gbm / peak, "bytes_per_site": 624}
+                                     "hbm_frac": gbm / peak, "bytes_per_site": 624,
+                                     "traffic": ncu_traffic("k_adjoint_ff_moments", lat.sites)}
         L.close()
     out["f64_ff"]["traffic"] = ncu_traffic("k_adjoint_ff", lat.sites)
     return out

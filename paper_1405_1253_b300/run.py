@@ -2,7 +2,7 @@
 the adjoint step to a seeded random field at the final state (FP64 storage only).
 
   python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
-  python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3
+  python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3 [--store moments]
 
 Used as the profiled program of the ncu summaries under profiles/.
 """
@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--adjoint", type=int, default=0, help="adjoint steps after the forward steps")
+    ap.add_argument("--store", default="states", choices=["states", "moments"],
+                    help="the adjoint reads the state (gathers f_t) or a moment record of the step")
     args = ap.parse_args()
     from . import lbm
     lat = W.Lattice(args.Lx, args.Lz, tau=args.tau, grav=args.grav, K=args.modes, sigma=args.sigma, seed=args.seed)
@@ -40,8 +42,14 @@ def main():
         f = L.populations_device().clone()
         gen = torch.Generator(device=f.device).manual_seed(args.seed)
         lam = [torch.rand(f.numel(), dtype=torch.float64, device=f.device, generator=gen), torch.empty_like(f)]
+        if args.store == "moments":
+            mom = [torch.empty(4 * lat.Lx * lat.Lz, dtype=torch.int64, device=f.device)]
+            L.record_moments(f, torch.empty_like(f), torch.empty_like(f), mom)
         for i in range(args.adjoint):
-            L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+            if args.store == "moments":
+                L.adjoint_chain_moments(mom, lam[i & 1], lam[(i + 1) & 1])
+            else:
+                L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
         L.sync()
         out.update(adjoint_steps=args.adjoint, lam_sum=float(lam[args.adjoint & 1].sum()))
     print(json.dumps(out))
