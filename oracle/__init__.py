@@ -73,6 +73,7 @@ def _load():
                 "oracle_widths": (i, [i, dp, d, d, d, dp, dp]),
                 "oracle_tent_widths": (None, [i, dp, d, d, d, dp]),
                 "oracle_adjoint_step": (None, [i, i, d, d, dp, dp, dp]),
+                "oracle_adjoint_step_thermal": (None, [i, i, d, d, dp, dp, dp, d, d]),
                 "oracle_loss_adjoint": (None, [i, i, dp, dp, dp]),
                 "oracle_init_adjoint": (None, [i, i, d, d, d, d, d, d, d, d, i,
                                                dp, dp, dp, dp, dp, dp, dp]),
@@ -235,12 +236,17 @@ def tent_widths(Tbar, Tu, Tm, Td) -> np.ndarray:
     return out
 
 
-def adjoint_step(f_t: np.ndarray, lam_next: np.ndarray, tau: float, grav: float) -> np.ndarray:
+def adjoint_step(f_t: np.ndarray, lam_next: np.ndarray, tau: float, grav: float, walls=None) -> np.ndarray:
+    """lam_t = P^T J_C^T lam_next at state f_t; walls=(T_bot, T_top) for the thermal walls."""
     lib = _load()
     f_t, lam_next = _f64(f_t), _f64(lam_next)
     _, Lx, Lz = f_t.shape
     out = np.empty_like(f_t)
-    lib.oracle_adjoint_step(Lx, Lz, float(tau), float(grav), _p(f_t), _p(lam_next), _p(out))
+    if walls is None:
+        lib.oracle_adjoint_step(Lx, Lz, float(tau), float(grav), _p(f_t), _p(lam_next), _p(out))
+    else:
+        lib.oracle_adjoint_step_thermal(Lx, Lz, float(tau), float(grav), _p(f_t), _p(lam_next), _p(out),
+                                        float(walls[0]), float(walls[1]))
     return out
 
 

@@ -637,16 +637,10 @@ void oracle_tent_widths(int Lz, const double *Tbar, double Tu, double Tm, double
  * P^T is applied through the explicit permutation obtained by running oracle_propagate
  * and oracle_bc on an array of source indices.
  * ------------------------------------------------------------------------- */
-void oracle_adjoint_step(int Lx, int Lz, double tau, double grav, const double *f_t,
-                         const double *lam_next, double *lam_out) {
-    oracle_setup();
-    size_t n = (size_t)NPOP * Lx * Lz;
-    double *g = (double *)malloc(n * sizeof(double));
-    double *mu = (double *)malloc(n * sizeof(double));
-    double *src = (double *)malloc(n * sizeof(double));
-    double *idxf = (double *)malloc(n * sizeof(double));
-    oracle_propagate(Lx, Lz, f_t, g);
-    oracle_bc(Lx, Lz, f_t, g);
+/* mu = J_C(g)^T lam_next at every site: the transpose of the collide's Jacobian, by the chain
+ * rule through rho, u, T of the shifted equilibrium (Sec. III.A). */
+static void collide_adjoint_sites(int Lx, int Lz, double tau, double grav, const double *g,
+                                  const double *lam_next, double *mu) {
     double om = 1.0 / tau;
     for (int x = 0; x < Lx; x++)
         for (int z = 0; z < Lz; z++) {
@@ -668,11 +662,86 @@ void oracle_adjoint_step(int Lx, int Lz, double tau, double grav, const double *
                 mu[ix(Lx, Lz, m, x, z)] = acc;
             }
         }
+}
+
+void oracle_adjoint_step(int Lx, int Lz, double tau, double grav, const double *f_t,
+                         const double *lam_next, double *lam_out) {
+    oracle_setup();
+    size_t n = (size_t)NPOP * Lx * Lz;
+    double *g = (double *)malloc(n * sizeof(double));
+    double *mu = (double *)malloc(n * sizeof(double));
+    double *src = (double *)malloc(n * sizeof(double));
+    double *idxf = (double *)malloc(n * sizeof(double));
+    oracle_propagate(Lx, Lz, f_t, g);
+    oracle_bc(Lx, Lz, f_t, g);
+    collide_adjoint_sites(Lx, Lz, tau, grav, g, lam_next, mu);
+    /* P^T of the permutation propagate + bc: each destination's mu goes back to its source */
     for (size_t i = 0; i < n; i++) idxf[i] = (double)i;
     oracle_propagate(Lx, Lz, idxf, src);
     oracle_bc(Lx, Lz, idxf, src);
     for (size_t i = 0; i < n; i++) lam_out[(size_t)src[i]] = mu[i];
     free(g); free(mu); free(src); free(idxf);
+}
+
+/* The adjoint step with the thermal walls of oracle_bc_thermal.  Propagate + thermal bc is
+ * linear but no longer a permutation: a destination pulled from a lattice entry passes its mu
+ * back to that entry; a destination pulled from a ghost row passes mu * f^eq_l(1,0,T_w) / in_w
+ * to the ghost column's density, which was out(x) / in_w, and so to every entry that the step
+ * moves into that ghost column (coefficient 1 in out(x)).  No destination pulls those
+ * entries, so they receive only the ghost column's sum. */
+static void thermal_wall_transpose(int Lx, int Lz, const double *mu, double *lam_out, double Tw, int top) {
+    double feq1[NPOP];
+    equilibrium_with_derivs(1.0, 0.0, 0.0, Tw, feq1, NULL, NULL);
+    const int g0 = top ? Lz : -3;
+    double in1 = 0.0;
+    for (int zg = g0; zg < g0 + 3; zg++)
+        for (int l = 0; l < NPOP; l++) {
+            int zd = zg + VEL[l][1];
+            if (zd >= 0 && zd < Lz) in1 += feq1[l];
+        }
+    double *omega = calloc((size_t)Lx, sizeof(double));
+    for (int x = 0; x < Lx; x++)
+        for (int l = 0; l < NPOP; l++)
+            for (int z = 0; z < Lz; z++) {
+                int zs = z - VEL[l][1];
+                if (zs < g0 || zs >= g0 + 3) continue;
+                int xs = ((x - VEL[l][0]) % Lx + Lx) % Lx;
+                omega[xs] += mu[ix(Lx, Lz, l, x, z)] * feq1[l] / in1;
+            }
+    for (int x = 0; x < Lx; x++)
+        for (int z = 0; z < Lz; z++)
+            for (int l = 0; l < NPOP; l++) {
+                int zd = z + VEL[l][1];
+                if (zd >= g0 && zd < g0 + 3) {
+                    int xd = ((x + VEL[l][0]) % Lx + Lx) % Lx;
+                    lam_out[ix(Lx, Lz, l, x, z)] += omega[xd];
+                }
+            }
+    free(omega);
+}
+
+void oracle_adjoint_step_thermal(int Lx, int Lz, double tau, double grav, const double *f_t,
+                                 const double *lam_next, double *lam_out, double T_bot, double T_top) {
+    oracle_setup();
+    size_t n = (size_t)NPOP * Lx * Lz;
+    double *g = (double *)malloc(n * sizeof(double));
+    double *mu = (double *)malloc(n * sizeof(double));
+    oracle_propagate(Lx, Lz, f_t, g);
+    oracle_bc_thermal(Lx, Lz, f_t, g, T_bot, T_top);
+    collide_adjoint_sites(Lx, Lz, tau, grav, g, lam_next, mu);
+    memset(lam_out, 0, n * sizeof(double));
+    /* lattice-to-lattice pulls */
+    for (int x = 0; x < Lx; x++)
+        for (int l = 0; l < NPOP; l++)
+            for (int z = 0; z < Lz; z++) {
+                int zs = z - VEL[l][1];
+                if (zs < 0 || zs >= Lz) continue;
+                int xs = ((x - VEL[l][0]) % Lx + Lx) % Lx;
+                lam_out[ix(Lx, Lz, l, xs, zs)] += mu[ix(Lx, Lz, l, x, z)];
+            }
+    thermal_wall_transpose(Lx, Lz, mu, lam_out, T_bot, 0);
+    thermal_wall_transpose(Lx, Lz, mu, lam_out, T_top, 1);
+    free(g); free(mu);
 }
 
 /* Adjoint of the loss readout: lam_N(l,x,z) = dL/dTbar(z) / Lx * dT(x,z)/df_l with

@@ -74,3 +74,54 @@ def test_loss_and_init_adjoint_chain_matches_finite_differences():
         fd_hi = (loss(a_lo, a_hi + e) - loss(a_lo, a_hi - e)) / (2 * h)
         assert abs(fd_lo - g_lo[k]) < 1e-5 * max(1.0, abs(fd_lo)), (k, fd_lo, g_lo[k])
         assert abs(fd_hi - g_hi[k]) < 1e-5 * max(1.0, abs(fd_hi)), (k, fd_hi, g_hi[k])
+
+
+WALLS = (1.04, 0.97)
+
+
+@pytest.mark.parametrize("Lx,Lz,tau,grav", [(3, 8, 0.8, 1e-4), (5, 7, 0.7, 5e-3)])
+def test_thermal_adjoint_step_dot_product(Lx, Lz, tau, grav):
+    """The adjoint step with thermal walls against a directional finite difference of the
+    oracle's thermal-wall step."""
+    rng = np.random.default_rng(11)
+    f = near_eq_state(Lx, Lz, 12)
+    lam = rng.standard_normal(f.shape)
+    v = rng.standard_normal(f.shape)
+    h = 1e-6
+    Jv = (oracle.step(f + h * v, tau, grav, walls=WALLS) - oracle.step(f - h * v, tau, grav, walls=WALLS)) / (2 * h)
+    lhs = np.sum(lam * Jv)
+    rhs = np.sum(oracle.adjoint_step(f, lam, tau, grav, walls=WALLS) * v)
+    assert abs(lhs - rhs) < 1e-7 * max(1.0, abs(lhs))
+
+
+def test_thermal_adjoint_columns_by_finite_differences():
+    """Columns of the thermal adjoint, including populations that leave through a wall (which
+    only the ghost densities take up) and wall-row destinations, by finite differences."""
+    Lx, Lz, tau, grav = 4, 8, 0.8, 1e-3
+    f = near_eq_state(Lx, Lz, 13)
+    rng = np.random.default_rng(14)
+    lam = rng.standard_normal(f.shape)
+    adj = oracle.adjoint_step(f, lam, tau, grav, walls=WALLS)
+    h = 1e-6
+    c, _ = oracle.velocities()
+    leaving = [np.ravel_multi_index((l, x, z), f.shape) for l in range(37) for x in range(Lx) for z in (0, 1, 2)
+               if z + c[l, 1] < 0]
+    picks = list(rng.choice(leaving, 10, replace=False)) + list(rng.choice(f.size, 20, replace=False))
+    for flat in picks:
+        e = np.zeros(f.size); e[flat] = h
+        e = e.reshape(f.shape)
+        fd = np.sum(lam * (oracle.step(f + e, tau, grav, walls=WALLS) - oracle.step(f - e, tau, grav, walls=WALLS))) / (2 * h)
+        assert abs(fd - adj.ravel()[flat]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_thermal_propagate_transpose_is_exact():
+    """With tau -> infinity and no gravity the collide is the identity, so the adjoint is the
+    transpose of propagate + thermal bc, a linear map: <P v, w> = <v, P^T w> to rounding."""
+    Lx, Lz = 5, 9
+    rng = np.random.default_rng(15)
+    f = near_eq_state(Lx, Lz, 16)
+    v, w = rng.standard_normal(f.shape), rng.standard_normal(f.shape)
+    Pv = oracle.bc_thermal(v, oracle.propagate(v), *WALLS)
+    PTw = oracle.adjoint_step(f, w, 1e15, 0.0, walls=WALLS)
+    lhs, rhs = np.sum(Pv * w), np.sum(v * PTw)
+    assert abs(lhs - rhs) < 1e-12 * np.sum(np.abs(Pv * w))
