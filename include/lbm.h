@@ -115,8 +115,9 @@ int lbm_step(lbm_ctx *c, int nsteps);
  * the ghost density of each column set so that the mass the step moves into the ghost
  * rows of that column equals the mass the ghost rows send into the lattice (total mass
  * is conserved).  With thermal walls, lbm_step_push, the slab decomposition, the
- * ensembles and the adjoint return LBM_ESTATE (they implement the bounce-back rule
- * only).  LBM_EINVAL for thermal outside {0, 1} or non-positive / non-finite wall
+ * ensembles, the moment records and the adjoint of LBM_F64 contexts return LBM_ESTATE
+ * (they implement the bounce-back rule only); the adjoint of LBM_F64_FF contexts follows
+ * the thermal rule.  LBM_EINVAL for thermal outside {0, 1} or non-positive / non-finite wall
  * temperatures.  Host only; takes effect from the next step.                          */
 int lbm_set_walls(lbm_ctx *c, int thermal, double T_bottom, double T_top);
 
@@ -211,7 +212,12 @@ int lbm_global_sums(lbm_ctx *c, double out[2]);
  * population, scaled per site by the largest exponent among its 37 lam_next values
  * (entries more than 2^74 below that maximum count as 0 in the collide term; results
  * agree with the native form to ~1e-15 of the site's largest |lam_next|).  Both assume
- * |u| well below 0.3 and finite inputs.  Asynchronous.                                */
+ * |u| well below 0.3 and finite inputs.  With thermal walls (lbm_set_walls; LBM_F64_FF
+ * only) propagate + bc is linear rather than a permutation: lam_out is its transpose, a
+ * population that leaves through a wall receiving the sum, over the destinations that pull
+ * from its ghost column, of their mu times f^eq_l(1, 0, T_w) / in_w; a second launch forms
+ * those sums in a fixed order, and the first call allocates 6*37*Lx doubles of scratch
+ * (LBM_ENOMEM if that fails).  Asynchronous.                                            */
 int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, double *lam_out);
 
 /* n adjoint steps in one call: with lam_a holding lam_n on entry, applies lbm_adjoint_step

@@ -43,9 +43,11 @@ class WidthGradient:
     prec "f64_ff" (float-float step and adjoint, the default) or "f64" (native FP64).
     store "moments" (f64_ff only, its default): the backward recomputes each segment keeping
     only the per-site moments the adjoint needs (32 bytes per site and step); "states": it
-    keeps the segment's states (296 bytes per site and step)."""
+    keeps the segment's states (296 bytes per site and step).  walls=(T_bottom, T_top):
+    thermal walls (lbm_set_walls) in the forward and the adjoint (f64_ff, states)."""
 
-    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None):
+    def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None,
+                 walls=None):
         import torch
         if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
             raise ValueError("nsteps must be a positive multiple of ckpt")
@@ -56,10 +58,12 @@ class WidthGradient:
         if prec not in ("f64", "f64_ff"):
             raise ValueError("the adjoint needs FP64 storage (prec 'f64' or 'f64_ff')")
         self.prec = prec
-        self.store = store or ("moments" if prec == "f64_ff" else "states")
-        if self.store not in ("moments", "states") or (self.store == "moments" and prec != "f64_ff"):
-            raise ValueError("store is 'states', or 'moments' with prec 'f64_ff'")
+        self.store = store or ("moments" if prec == "f64_ff" and walls is None else "states")
+        if self.store not in ("moments", "states") or (self.store == "moments" and (prec != "f64_ff" or walls)):
+            raise ValueError("store is 'states', or 'moments' with prec 'f64_ff' and bounce-back walls")
         self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
+        if walls is not None:                      # thermal walls at (T_bottom, T_top)
+            self.L.set_walls(True, *walls)
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
         self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]

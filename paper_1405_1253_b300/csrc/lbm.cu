@@ -23,6 +23,7 @@
 #include "adjoint.cuh"
 #include "adjoint_ff.cuh"
 #include "walls.cuh"
+#include "adjoint_walls.cuh"
 #include "ensemble.cuh"
 
 using namespace lbm;
@@ -195,6 +196,7 @@ struct lbm_ctx {
     // wall rule: 0 half-way bounce-back, 1 thermal walls (lbm_set_walls)
     int thermal = 0;
     ThermalWall tw{};
+    double* gmu = nullptr;      // 6 * Q * Lx: ghost-pull scratch of the thermal-wall adjoint
 };
 
 static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
@@ -228,7 +230,7 @@ static int ensure_part(lbm_ctx* c, size_t n) {
 
 static void free_ctx(lbm_ctx* c) {
     if (!c) return;
-    void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err};
+    void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err, c->gmu};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; k++) {
@@ -830,7 +832,9 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
 // ---------------------------------------------------------------------------------
 static void launch_adjoint(const lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out,
                            const StepParams& p) {
-    if (c->prec == LBM_F64_FF) {
+    if (c->thermal) {               // LBM_F64_FF with its ghost scratch (adjoint_walls_ready)
+        launch_adjoint_ff_thermal(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, c->tw, c->gmu, c->stream);
+    } else if (c->prec == LBM_F64_FF) {
         launch_adjoint_ff(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z),
                           c->stream);
     } else {
@@ -839,12 +843,23 @@ static void launch_adjoint(const lbm_ctx* c, const double* f_t, const double* la
     }
 }
 
+// The adjoint with the context's wall rule can run: thermal walls need LBM_F64_FF and the
+// ghost-pull scratch (allocated here on first use).
+static int adjoint_walls_ready(lbm_ctx* c) {
+    if (!c->thermal) return LBM_OK;
+    if (c->prec != LBM_F64_FF) return fail(LBM_ESTATE, "the adjoint with thermal walls needs an LBM_F64_FF context");
+    if (!c->gmu && dev_malloc(&c->gmu, (size_t)6 * Q * c->Lx * sizeof(double)) != cudaSuccess)
+        return fail(LBM_ENOMEM, "thermal-wall adjoint scratch allocation failed");
+    return LBM_OK;
+}
+
 int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
     if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
     if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
-    NEED_BOUNCE_BACK(c, "the adjoint step");
     if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
     DeviceGuard dg(c->device);
+    int rc = adjoint_walls_ready(c);
+    if (rc) return rc;
     launch_adjoint(c, f_t, lam_next, lam_out, step_params(c));
     LAUNCH_CHECK();
     return LBM_OK;
@@ -854,13 +869,14 @@ int lbm_adjoint_chain(lbm_ctx* c, const double* const* states, int n, double* la
     if (!c || !states || !lam_a || !lam_b || !out_index) return fail(LBM_EINVAL, "NULL argument");
     if (n < 0) return fail(LBM_EINVAL, "n < 0");
     if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
-    NEED_BOUNCE_BACK(c, "the adjoint step");
     if (lam_a == lam_b) return fail(LBM_EINVAL, "lam_a and lam_b must differ");
     for (int j = 0; j < n; j++) {
         if (!states[j]) return fail(LBM_EINVAL, "state %d is NULL", j);
         if (states[j] == lam_a || states[j] == lam_b) return fail(LBM_EINVAL, "state %d aliases an adjoint buffer", j);
     }
     DeviceGuard dg(c->device);
+    int rc = adjoint_walls_ready(c);
+    if (rc) return rc;
     const StepParams p = step_params(c);
     double* lam[2] = {lam_a, lam_b};
     int cur = 0;

@@ -65,6 +65,9 @@ def exercise():
             T.init_from(W.Lattice(Lx, Lz, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=24))
             T.set_walls(True, 1.05, 0.95)
             T.step(2)
+            if prec == "f64_ff":                  # the thermal-wall adjoint and its ghost sums
+                f = T.populations_device().clone()
+                T.adjoint_step(f, torch.rand_like(f), torch.empty_like(f))
     H = lbm.Lattice(16, 48, 0.8, 1e-4, prec="f64_ff")
     a = np.ones(37 * 16 * 48)
     b = np.empty_like(a)

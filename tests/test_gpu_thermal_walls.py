@@ -1,7 +1,8 @@
 """Thermal walls on the GPU (scope row N3): lbm_set_walls against the oracle's thermal-wall
 step, in every precision, on the parity workload, the edge shapes and a ragged lattice;
 exact mass conservation, the rest state at the wall temperature, the switch back to
-bounce-back, host stepping, and the entry points that refuse thermal walls."""
+bounce-back, host stepping, and the entry points that refuse thermal walls (the adjoint with
+thermal walls: test_gpu_thermal_adjoint.py)."""
 import numpy as np
 import pytest
 
@@ -126,7 +127,8 @@ def test_entry_points_refuse_thermal_walls(lbm):
     assert e.value.code == lbm.LBM_EINVAL
     L.set_walls(True, 1.05, 0.95)
     x = L.populations_device().clone()
-    for call in (lambda: L.step_push(1), lambda: L.adjoint_step(x, x.clone(), torch.empty_like(x)),
+    mom = [torch.empty(4 * lat.Lx * lat.Lz, dtype=torch.int64, device=x.device)]
+    for call in (lambda: L.step_push(1), lambda: L.record_moments(x, x.clone(), x.clone(), mom),
                  lambda: lbm.Slabs(L, 4), lambda: lbm.Ensemble([L]).step(1)):
         with pytest.raises(lbm.LBMError) as e:
             call()
