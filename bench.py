@@ -392,9 +392,25 @@ def bench_walls(torch, lbm, lat, steps, stream):
             e1.record(stream)
             e1.synchronize()
             res["thermal" if thermal else "bounce_back"] = lat.sites * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
-        L.close()
         out[prec] = {"bounce_back_mlups": res["bounce_back"], "thermal_mlups": res["thermal"],
                      "thermal_over_bounce_back": res["thermal"] / res["bounce_back"]}
+        if prec == "f64_ff":                 # the adjoint step under each wall rule
+            f = L.populations_device().clone()
+            lam = [torch.rand_like(f), torch.empty_like(f)]
+            for thermal in (False, True):
+                L.set_walls(thermal, lat.T_d, lat.T_u)
+                for i in range(3):
+                    L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for i in range(20):
+                    L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
+                e1.record(stream)
+                e1.synchronize()
+                key = "adjoint_thermal_mlups" if thermal else "adjoint_bounce_back_mlups"
+                out[prec][key] = lat.sites * 20 / (e0.elapsed_time(e1) * 1e-3) / 1e6
+        L.close()
     return out
 
 
