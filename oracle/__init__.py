@@ -77,6 +77,8 @@ def _load():
                 "oracle_loss_adjoint": (None, [i, i, dp, dp, dp]),
                 "oracle_init_adjoint": (None, [i, i, d, d, d, d, d, d, d, d, i,
                                                dp, dp, dp, dp, dp, dp, dp]),
+                "oracle_init_adjoint_phases": (None, [i, i, d, d, d, d, d, d, d, d, i,
+                                                      dp, dp, dp, dp, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -257,6 +259,20 @@ def loss_adjoint(f: np.ndarray, dL_dTbar) -> np.ndarray:
     out = np.empty_like(f)
     lib.oracle_loss_adjoint(Lx, Lz, _p(f), _p(dL_dTbar), _p(out))
     return out
+
+
+def init_adjoint_phases(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt,
+                        amp_lo, ph_lo, amp_hi, ph_hi, lam0):
+    """dL/dphi of the lower and upper interface modes, given lam0 = dL/df_0."""
+    lib = _load()
+    amp_lo, ph_lo, amp_hi, ph_hi, lam0 = map(_f64, (amp_lo, ph_lo, amp_hi, ph_hi, lam0))
+    K = len(amp_lo)
+    dlo, dhi = np.zeros(K), np.zeros(K)
+    lib.oracle_init_adjoint_phases(int(Lx), int(Lz), float(grav), float(Tu), float(Tm), float(Td),
+                                   float(zlo0), float(zhi0), float(rho_ref), float(wt), K,
+                                   _p(amp_lo), _p(ph_lo), _p(amp_hi), _p(ph_hi), _p(lam0),
+                                   _p(dlo), _p(dhi))
+    return dlo, dhi
 
 
 def init_adjoint(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt,

@@ -765,14 +765,14 @@ void oracle_loss_adjoint(int Lx, int Lz, const double *f, const double *dL_dTbar
  * df0/dz_lo = df^eq/drho drho/dz_lo + df^eq/dT dT/dz_lo, rho = p/T; p depends on z_lo
  * above z_lo through p(z_lo), continuity making the layer boundaries themselves contribute
  * nothing. */
-void oracle_init_adjoint(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
-                         double zlo0, double zhi0, double rho_ref, double wt, int K,
-                         const double *amp_lo, const double *ph_lo,
-                         const double *amp_hi, const double *ph_hi,
-                         const double *lam0, double *dA_lo, double *dA_hi) {
-    oracle_setup();
+/* dL/dz_lo(x) and dL/dz_hi(x) for every column: the adjoint of the initial state (a function
+ * of the interface heights of the column) applied to lam0 = dL/df_0. */
+static void init_adjoint_columns(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
+                                 double zlo0, double zhi0, double rho_ref, double wt, int K,
+                                 const double *amp_lo, const double *ph_lo,
+                                 const double *amp_hi, const double *ph_hi,
+                                 const double *lam0, double *gcol_lo, double *gcol_hi) {
     double r = R_LATTICE;
-    for (int k = 0; k < K; k++) { dA_lo[k] = 0.0; dA_hi[k] = 0.0; }
     for (int x = 0; x < Lx; x++) {
         double zl = interface_height(zlo0, K, amp_lo, ph_lo, x, Lx);
         double zh = interface_height(zhi0, K, amp_hi, ph_hi, x, Lx);
@@ -796,9 +796,45 @@ void oracle_init_adjoint(int Lx, int Lz, double grav, double Tu, double Tm, doub
                 gh += lamv * (feq[l] / rho * drho_dzh + dfdT[l] * dT_dzh);
             }
         }
-        for (int k = 0; k < K; k++) {
-            dA_lo[k] += gl * cos(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_lo[k]);
-            dA_hi[k] += gh * cos(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_hi[k]);
-        }
+        gcol_lo[x] = gl;
+        gcol_hi[x] = gh;
     }
+}
+
+/* dL/dA_k = sum_x dL/dz(x) cos(2 pi k x / Lx + phi_k) (the interface heights of Sec. I). */
+void oracle_init_adjoint(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
+                         double zlo0, double zhi0, double rho_ref, double wt, int K,
+                         const double *amp_lo, const double *ph_lo,
+                         const double *amp_hi, const double *ph_hi,
+                         const double *lam0, double *dA_lo, double *dA_hi) {
+    oracle_setup();
+    double *gl = malloc((size_t)Lx * sizeof(double)), *gh = malloc((size_t)Lx * sizeof(double));
+    init_adjoint_columns(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt, K, amp_lo, ph_lo, amp_hi, ph_hi,
+                         lam0, gl, gh);
+    for (int k = 0; k < K; k++) { dA_lo[k] = 0.0; dA_hi[k] = 0.0; }
+    for (int x = 0; x < Lx; x++)
+        for (int k = 0; k < K; k++) {
+            dA_lo[k] += gl[x] * cos(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_lo[k]);
+            dA_hi[k] += gh[x] * cos(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_hi[k]);
+        }
+    free(gl); free(gh);
+}
+
+/* dL/dphi_k = -A_k sum_x dL/dz(x) sin(2 pi k x / Lx + phi_k). */
+void oracle_init_adjoint_phases(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
+                                double zlo0, double zhi0, double rho_ref, double wt, int K,
+                                const double *amp_lo, const double *ph_lo,
+                                const double *amp_hi, const double *ph_hi,
+                                const double *lam0, double *dph_lo, double *dph_hi) {
+    oracle_setup();
+    double *gl = malloc((size_t)Lx * sizeof(double)), *gh = malloc((size_t)Lx * sizeof(double));
+    init_adjoint_columns(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt, K, amp_lo, ph_lo, amp_hi, ph_hi,
+                         lam0, gl, gh);
+    for (int k = 0; k < K; k++) { dph_lo[k] = 0.0; dph_hi[k] = 0.0; }
+    for (int x = 0; x < Lx; x++)
+        for (int k = 0; k < K; k++) {
+            dph_lo[k] -= amp_lo[k] * gl[x] * sin(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_lo[k]);
+            dph_hi[k] -= amp_hi[k] * gh[x] * sin(2.0 * M_PI * (k + 1) * x / (double)Lx + ph_hi[k]);
+        }
+    free(gl); free(gh);
 }

@@ -125,3 +125,33 @@ def test_thermal_propagate_transpose_is_exact():
     PTw = oracle.adjoint_step(f, w, 1e15, 0.0, walls=WALLS)
     lhs, rhs = np.sum(Pv * w), np.sum(v * PTw)
     assert abs(lhs - rhs) < 1e-12 * np.sum(np.abs(Pv * w))
+
+
+def test_phase_gradient_chain_matches_finite_differences():
+    """d(L_u + L_d)/dphi for a short run: the adjoint chain (init_adjoint_phases) against
+    centred finite differences in each phase of both fronts."""
+    Lx, Lz, grav, tau, nsteps, K = 12, 48, 1e-3, 0.8, 6, 2
+    rng = np.random.default_rng(6)
+    a_lo, a_hi = rng.normal(0, 1, K), rng.normal(0, 1, K)
+    p_lo, p_hi = rng.uniform(0, 2 * np.pi, K), rng.uniform(0, 2 * np.pi, K)
+    args = (Lx, Lz, grav, TU, TM, TD, Lz / 3, 2 * Lz / 3, 1.0, 3.0)
+
+    def loss(pl, ph):
+        f = oracle.step(oracle.init_layers(*args, a_lo, pl, a_hi, ph), tau, grav, nsteps)
+        return oracle.widths(oracle.row_mean_T(f), TU, TM, TD).sum()
+
+    states = [oracle.init_layers(*args, a_lo, p_lo, a_hi, p_hi)]
+    for _ in range(nsteps):
+        states.append(oracle.step(states[-1], tau, grav))
+    _, dL = oracle.widths(oracle.row_mean_T(states[-1]), TU, TM, TD, with_grad=True)
+    lam = oracle.loss_adjoint(states[-1], dL)
+    for t in range(nsteps - 1, -1, -1):
+        lam = oracle.adjoint_step(states[t], lam, tau, grav)
+    g_lo, g_hi = oracle.init_adjoint_phases(*args, a_lo, p_lo, a_hi, p_hi, lam)
+    h = 1e-6
+    for k in range(K):
+        e = np.zeros(K); e[k] = h
+        fd_lo = (loss(p_lo + e, p_hi) - loss(p_lo - e, p_hi)) / (2 * h)
+        fd_hi = (loss(p_lo, p_hi + e) - loss(p_lo, p_hi - e)) / (2 * h)
+        assert abs(fd_lo - g_lo[k]) < 1e-5 * max(1.0, abs(fd_lo)), (k, fd_lo, g_lo[k])
+        assert abs(fd_hi - g_hi[k]) < 1e-5 * max(1.0, abs(fd_hi)), (k, fd_hi, g_hi[k])
