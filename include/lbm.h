@@ -255,6 +255,13 @@ int lbm_loss_adjoint(lbm_ctx *c, const double *f, const double *dL_dTbar, double
 int lbm_init_adjoint(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,
                      double *dA_lo, double *dA_hi);
 
+/* lbm_init_adjoint plus, when dph_lo and dph_hi are given (both or neither), the gradient with
+ * respect to the mode phases: the interfaces z(x) = z0 + sum_k A_k cos(2 pi k x / Lx + phi_k)
+ * (Sec. I) give dL/dphi_k = -A_k sum_x dL/dz(x) sin(2 pi k x / Lx + phi_k).  Host arrays of
+ * n_modes doubles.  Synchronises.                                                         */
+int lbm_init_adjoint_full(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,
+                          double *dA_lo, double *dA_hi, double *dph_lo, double *dph_hi);
+
 /* Wait for all work queued by this context; reports deferred kernel-side errors.     */
 int lbm_sync(lbm_ctx *c);
 

@@ -81,34 +81,38 @@ class WidthGradient:
                                   state_bytes=8 * n)
         self._amps = None
 
-    def _init(self, amp_lo, amp_hi):
-        m = self.lat.modes()
+    def _init(self, amp_lo, amp_hi, ph_lo, ph_hi):
         lat = self.lat
         self.L.init_layers(lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi, lat.rho_ref, lat.tanh_w,
-                           amp_lo, m.ph_lo, amp_hi, m.ph_hi)
+                           amp_lo, ph_lo, amp_hi, ph_hi)
 
-    def forward(self, amp_lo, amp_hi) -> float:
-        """Run N steps from the initial state with these amplitudes; returns L_u + L_d."""
+    def forward(self, amp_lo, amp_hi, ph_lo=None, ph_hi=None) -> float:
+        """Run N steps from the initial state with these amplitudes (and phases; by default
+        the description's); returns L_u + L_d."""
         torch = self.torch
         lat = self.lat
+        m = lat.modes()
         amp_lo = np.asarray(amp_lo, dtype=np.float64)
         amp_hi = np.asarray(amp_hi, dtype=np.float64)
+        ph_lo = np.asarray(m.ph_lo if ph_lo is None else ph_lo, dtype=np.float64)
+        ph_hi = np.asarray(m.ph_hi if ph_hi is None else ph_hi, dtype=np.float64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        self._init(amp_lo, amp_hi)
+        self._init(amp_lo, amp_hi, ph_lo, ph_hi)
         for s in range(self.N // self.K):
             self.L.populations_device(self.ckpts[s])
             self.L.step(self.K)
         widths, dL = self.L.widths(lat.T_u, lat.T_m, lat.T_d, with_grad=True)
         self.stats.forward_s = time.perf_counter() - t0
         self.stats.widths = widths
-        self._amps = (amp_lo, amp_hi)
+        self._amps = (amp_lo, amp_hi, ph_lo, ph_hi)
         self._dL = dL
         self._fN = self.L.populations_device()
         return float(widths.sum())
 
     def backward(self, grad_out: float = 1.0):
-        """dL/damp_lo, dL/damp_hi for the last forward call (scaled by grad_out)."""
+        """dL/damp_lo, dL/damp_hi for the last forward call (scaled by grad_out); the phase
+        gradients dL/dphi_lo, dL/dphi_hi are left in self.grad_phases."""
         torch = self.torch
         lat = self.lat
         if self._amps is None:
@@ -134,10 +138,11 @@ class WidthGradient:
             if flip == 1:
                 cur, nxt = nxt, cur
             self.stats.adjoint_steps += self.K
-        amp_lo, amp_hi = self._amps
-        m = lat.modes()
-        g_lo, g_hi = self.L.init_adjoint(cur, lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi, lat.rho_ref,
-                                         lat.tanh_w, amp_lo, m.ph_lo, amp_hi, m.ph_hi)
+        amp_lo, amp_hi, ph_lo, ph_hi = self._amps
+        g_lo, g_hi, p_lo, p_hi = self.L.init_adjoint(cur, lat.T_u, lat.T_m, lat.T_d, lat.z_lo, lat.z_hi,
+                                                     lat.rho_ref, lat.tanh_w, amp_lo, ph_lo, amp_hi, ph_hi,
+                                                     phases=True)
+        self.grad_phases = (p_lo, p_hi)
         self.stats.backward_s = time.perf_counter() - t0
         return g_lo, g_hi
 

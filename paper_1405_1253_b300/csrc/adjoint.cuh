@@ -200,32 +200,41 @@ k_init_adjoint_columns(const double* __restrict__ lam0, const double* __restrict
     }
 }
 
-// dL/dA_k = sum_x colred[x] cos(2 pi k x / Lx + phi_k), one block per mode.
+// dL/dA_k = sum_x colred[x] cos(2 pi k x / Lx + phi_k) and
+// dL/dphi_k = -A_k sum_x colred[x] sin(2 pi k x / Lx + phi_k), one block per mode; out holds
+// dA_lo, dA_hi, dphi_lo, dphi_hi (K each).
 __global__ void __launch_bounds__(128)
 k_init_adjoint_modes(const double* __restrict__ colred, const double* __restrict__ modes, InitParams ip,
                      double* __restrict__ out) {
-    __shared__ double sm[2][128];
+    __shared__ double sm[4][128];
     const int k = blockIdx.x;
     const double ph_lo = modes[ip.K + k], ph_hi = modes[3 * ip.K + k];
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
     for (int x = threadIdx.x; x < ip.Lx; x += 128) {
         const double arg = 2.0 * M_PI * (double)(k + 1) * (double)x / (double)ip.Lx;
-        a += colred[x] * cos(arg + ph_lo);
-        b += colred[ip.Lx + x] * cos(arg + ph_hi);
+        double s_lo, c_lo, s_hi, c_hi;
+        sincos(arg + ph_lo, &s_lo, &c_lo);
+        sincos(arg + ph_hi, &s_hi, &c_hi);
+        a += colred[x] * c_lo;
+        b += colred[ip.Lx + x] * c_hi;
+        c += colred[x] * s_lo;
+        d += colred[ip.Lx + x] * s_hi;
     }
     sm[0][threadIdx.x] = a;
     sm[1][threadIdx.x] = b;
+    sm[2][threadIdx.x] = c;
+    sm[3][threadIdx.x] = d;
     __syncthreads();
     for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sm[0][threadIdx.x] += sm[0][threadIdx.x + w];
-            sm[1][threadIdx.x] += sm[1][threadIdx.x + w];
-        }
+        if (threadIdx.x < w)
+            for (int j = 0; j < 4; j++) sm[j][threadIdx.x] += sm[j][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         out[k] = sm[0][0];
         out[ip.K + k] = sm[1][0];
+        out[2 * ip.K + k] = -modes[k] * sm[2][0];
+        out[3 * ip.K + k] = -modes[2 * ip.K + k] * sm[3][0];
     }
 }
 

@@ -946,7 +946,8 @@ int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double
     return LBM_OK;
 }
 
-int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi) {
+int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi,
+                          double* dph_lo, double* dph_hi) {
     if (!c || !lam0) return fail(LBM_EINVAL, "NULL argument");
     if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     DeviceGuard dg(c->device);
@@ -954,20 +955,33 @@ int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, d
     int rc = fill_init_params(c, d, &ip);
     if (rc) return rc;
     if (d->n_modes > 0 && (!dA_lo || !dA_hi)) return fail(LBM_EINVAL, "NULL gradient outputs");
+    if ((dph_lo == nullptr) != (dph_hi == nullptr)) return fail(LBM_EINVAL, "give both phase outputs or neither");
     k_interfaces<<<(c->Lx + 127) / 128, 128, 0, c->stream>>>(c->zcol, c->modes, ip);
     LAUNCH_CHECK();
     k_init_adjoint_columns<<<c->Lx, 128, 0, c->stream>>>(lam0, c->zcol, ip, c->colred);
     LAUNCH_CHECK();
     if (d->n_modes == 0) return lbm_sync(c);
-    rc = ensure_part(c, 2 * (size_t)d->n_modes);
+    const int K = d->n_modes;
+    rc = ensure_part(c, 4 * (size_t)K);
     if (rc) return rc;
-    k_init_adjoint_modes<<<d->n_modes, 128, 0, c->stream>>>(c->colred, c->modes, ip, c->part);
+    k_init_adjoint_modes<<<K, 128, 0, c->stream>>>(c->colred, c->modes, ip, c->part);
     LAUNCH_CHECK();
-    std::vector<double> h(2 * (size_t)d->n_modes);
+    std::vector<double> h(4 * (size_t)K);
     CU(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < d->n_modes; k++) { dA_lo[k] = h[k]; dA_hi[k] = h[d->n_modes + k]; }
+    for (int k = 0; k < K; k++) {
+        dA_lo[k] = h[k];
+        dA_hi[k] = h[K + k];
+        if (dph_lo) {
+            dph_lo[k] = h[2 * K + k];
+            dph_hi[k] = h[3 * K + k];
+        }
+    }
     return LBM_OK;
+}
+
+int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi) {
+    return lbm_init_adjoint_full(c, d, lam0, dA_lo, dA_hi, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -62,6 +62,7 @@ _SIGS = {
     "lbm_adjoint_step": (_i, [_vp, _vp, _vp, _vp]),
     "lbm_loss_adjoint": (_i, [_vp, _vp, _dp, _vp]),
     "lbm_init_adjoint": (_i, [_vp, ctypes.POINTER(LayersDesc), _vp, _dp, _dp]),
+    "lbm_init_adjoint_full": (_i, [_vp, ctypes.POINTER(LayersDesc), _vp, _dp, _dp, _dp, _dp]),
     "lbm_sync": (_i, [_vp]),
     "lbm_lattice": (_i, [_ip, _dp, _dp]),
     "lbm_row_mean_T_noalloc": (_i, [_vp, _i, _i, _vp, _vp]),
@@ -327,12 +328,20 @@ class Lattice:
         assert dL.size == self.Lz
         _check(_lib.lbm_loss_adjoint(self.ctx, f.data_ptr(), _dptr(dL), lam_out.data_ptr()))
 
-    def init_adjoint(self, lam0, T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi):
+    def init_adjoint(self, lam0, T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi,
+                     phases: bool = False):
+        """dL/dA of both fronts from lam0 = dL/df_0; with phases=True also dL/dphi
+        (returns dA_lo, dA_hi, dphi_lo, dphi_hi)."""
         d, keep = layers_desc(T_u, T_m, T_d, z_lo, z_hi, rho_ref, tanh_w, amp_lo, ph_lo, amp_hi, ph_hi)
         K = d.n_modes
         dlo, dhi = np.zeros(max(K, 1)), np.zeros(max(K, 1))
-        _check(_lib.lbm_init_adjoint(self.ctx, ctypes.byref(d), lam0.data_ptr(), _dptr(dlo), _dptr(dhi)))
-        return dlo[:K], dhi[:K]
+        if not phases:
+            _check(_lib.lbm_init_adjoint(self.ctx, ctypes.byref(d), lam0.data_ptr(), _dptr(dlo), _dptr(dhi)))
+            return dlo[:K], dhi[:K]
+        plo, phi = np.zeros(max(K, 1)), np.zeros(max(K, 1))
+        _check(_lib.lbm_init_adjoint_full(self.ctx, ctypes.byref(d), lam0.data_ptr(), _dptr(dlo), _dptr(dhi),
+                                          _dptr(plo), _dptr(phi)))
+        return dlo[:K], dhi[:K], plo[:K], phi[:K]
 
 
 class Ensemble:

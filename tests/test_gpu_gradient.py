@@ -95,3 +95,37 @@ def test_moment_store_gives_the_same_gradient(adj):
         out.append(np.concatenate(drv.backward()))
         drv.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_phase_gradient_matches_oracle_chain_and_finite_differences(adj):
+    """dL/dphi from the driver (init adjoint with phases) against the oracle's chain, and
+    against centred differences of the GPU forward in each phase."""
+    lat = W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=21)
+    nsteps, ckpt = 6, 3
+    drv = adj.WidthGradient(lat, nsteps, ckpt)
+    m = lat.modes()
+    drv.forward(m.amp_lo, m.amp_hi)
+    drv.backward()
+    p_lo, p_hi = drv.grad_phases
+    a = lat.layer_args()
+    states = [oracle.init_layers(lat.Lx, lat.Lz, **a)]
+    for _ in range(nsteps):
+        states.append(oracle.step(states[-1], lat.tau, lat.grav))
+    _, dL = oracle.widths(oracle.row_mean_T(states[-1]), lat.T_u, lat.T_m, lat.T_d, with_grad=True)
+    lam = oracle.loss_adjoint(states[-1], dL)
+    for t in range(nsteps - 1, -1, -1):
+        lam = oracle.adjoint_step(states[t], lam, lat.tau, lat.grav)
+    o_lo, o_hi = oracle.init_adjoint_phases(lat.Lx, lat.Lz, **a, lam0=lam)
+    np.testing.assert_allclose(p_lo, o_lo, rtol=1e-9, atol=1e-12 * np.abs(o_lo).max())
+    np.testing.assert_allclose(p_hi, o_hi, rtol=1e-9, atol=1e-12 * np.abs(o_hi).max())
+    h = 1e-6
+    for k in range(lat.K):
+        e = np.zeros(lat.K)
+        e[k] = h
+        fd_lo = (drv.forward(m.amp_lo, m.amp_hi, m.ph_lo + e, m.ph_hi)
+                 - drv.forward(m.amp_lo, m.amp_hi, m.ph_lo - e, m.ph_hi)) / (2 * h)
+        fd_hi = (drv.forward(m.amp_lo, m.amp_hi, m.ph_lo, m.ph_hi + e)
+                 - drv.forward(m.amp_lo, m.amp_hi, m.ph_lo, m.ph_hi - e)) / (2 * h)
+        assert abs(fd_lo - p_lo[k]) < 1e-4 * max(1.0, abs(fd_lo))
+        assert abs(fd_hi - p_hi[k]) < 1e-4 * max(1.0, abs(fd_hi))
+    drv.close()
