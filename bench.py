@@ -257,13 +257,14 @@ def bench_ensemble(torch, lbm, prec, steps, stream):
 def bench_adjoint(torch):
     """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and backward
     (recompute + adjoint) wall times and device memory, for both backward stores of the
-    float-float driver (moment records, segment states)."""
+    float-float driver (moment records, segment states) and for an FP32-storage run."""
     from paper_1405_1253_b300 import adjoint
     lat = W.GRADIENT_256x512
     out = {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (f64_ff)"}
     m = lat.modes()
-    for store in ("moments", "states"):
-        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, store=store)
+    for store, prec in (("moments", "f64_ff"), ("states", "f64_ff"), ("states", "f32")):
+        key = store if prec == "f64_ff" else "f32"
+        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store)
         drv.forward(m.amp_lo, m.amp_hi)      # warm
         drv.backward()
         drv.forward(m.amp_lo, m.amp_hi)
@@ -271,7 +272,7 @@ def bench_adjoint(torch):
         st = drv.stats
         drv.close()
         mem = st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes
-        out[store] = {"forward_s": st.forward_s, "backward_s": st.backward_s,
+        out[key] = {"forward_s": st.forward_s, "backward_s": st.backward_s,
                       "backward_over_forward": st.backward_s / st.forward_s,
                       "memory_bytes": mem, "forward_memory_bytes": 2 * st.state_bytes,
                       "memory_over_forward": mem / (2 * st.state_bytes),
@@ -331,13 +332,14 @@ def bench_push(torch, lbm, lat, steps, stream):
 
 
 def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
-    """The adjoint step kernel alone on the 1024x2048 state, float-float and native FP64:
-    it reads f_t and lam_{t+1} and writes lam_t, 3 x 296 = 888 algorithmic bytes per site."""
+    """The adjoint step kernel alone on the 1024x2048 state, float-float, native FP64 and FP32:
+    it reads f_t and lam_{t+1} and writes lam_t, 3 x 37 populations per site (888 B in FP64
+    storage, 444 B in FP32)."""
     out = {"workload": f"{lat.Lx}x{lat.Lz}, FP64 storage, {steps} adjoint steps", "bytes_per_site": 888}
-    for prec in ("f64_ff", "f64"):
+    for prec in ("f64_ff", "f64", "f32"):
         L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
         L.init_from(lat)
-        f = L.populations_device().clone()
+        f = L.current().clone()              # the state in the storage precision
         lam = [torch.rand_like(f), torch.empty_like(f)]
         for i in range(3):
             L.adjoint_step(f, lam[i & 1], lam[(i + 1) & 1])
@@ -349,8 +351,10 @@ def bench_adjoint_kernel(torch, lbm, lat, steps, stream, peak):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        gbs = 888 * lat.sites / (ms * 1e-3) / 1e9
-        out[prec] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+        bps = 3 * Q * BYTES_PER_POP[prec]                # 888 B/site (FP64 storage), 444 (FP32)
+        gbs = bps * lat.sites / (ms * 1e-3) / 1e9
+        out[prec] = {"ms": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak,
+                     "bytes_per_site": bps}
         if prec == "f64_ff":
             # the same adjoint with f_t given by its moment record: 32 + 296 + 296 = 624 B/site
             wa, wb = torch.empty_like(f), torch.empty_like(f)

@@ -202,13 +202,13 @@ int lbm_row_stats(lbm_ctx *c, double *T_mean, double *T_rms, double *Ek_mean, do
  * finite.                                                                             */
 int lbm_global_sums(lbm_ctx *c, double out[2]);
 
-/* Adjoint of one step (FP64 storage: LBM_F64 or LBM_F64_FF; LBM_ESTATE for LBM_F32).
- * With f_{t+1} = C(P f_t), P the propagate+bc permutation and C the pointwise collide
- * (Eq. (LBE) with the shifted equilibrium of Sec. III.A):
+/* Adjoint of one step.  With f_{t+1} = C(P f_t), P the propagate+bc permutation and C the
+ * pointwise collide (Eq. (LBE) with the shifted equilibrium of Sec. III.A):
  *   lam_out = P^T J_C(P f_t)^T lam_next.
- * f_t, lam_next, lam_out: device arrays of 37*Lx*Lz doubles in the storage layout;
- * lam_out must not alias the other two.  LBM_F64 evaluates the Jacobian product in
- * native FP64; LBM_F64_FF in float-float on the FP32 pipes with one FP64 FMA per
+ * f_t, lam_next, lam_out: device arrays of 37*Lx*Lz populations in the context's storage
+ * precision and layout (double for LBM_F64 / LBM_F64_FF, float for LBM_F32); lam_out must
+ * not alias the other two.  LBM_F64 evaluates the Jacobian product in native FP64, LBM_F32
+ * in FP32 (the gradient of an FP32 run to FP32 rounding); LBM_F64_FF in float-float on the FP32 pipes with one FP64 FMA per
  * population, scaled per site by the largest exponent among its 37 lam_next values
  * (entries more than 2^74 below that maximum count as 0 in the collide term; results
  * agree with the native form to ~1e-15 of the site's largest |lam_next|).  Both assume
@@ -218,14 +218,14 @@ int lbm_global_sums(lbm_ctx *c, double out[2]);
  * from its ghost column, of their mu times f^eq_l(1, 0, T_w) / in_w; a second launch forms
  * those sums in a fixed order, and the first call allocates 6*37*Lx doubles of scratch
  * (LBM_ENOMEM if that fails).  Asynchronous.                                            */
-int lbm_adjoint_step(lbm_ctx *c, const double *f_t, const double *lam_next, double *lam_out);
+int lbm_adjoint_step(lbm_ctx *c, const void *f_t, const void *lam_next, void *lam_out);
 
 /* n adjoint steps in one call: with lam_a holding lam_n on entry, applies lbm_adjoint_step
  * for t = n - 1 down to 0 with f_t = states[t], ping-ponging between lam_a and lam_b;
- * *out_index = 0 if lam_0 ends in lam_a, 1 if in lam_b.  The states (device, FP64 layout)
- * must not alias lam_a or lam_b.  Same precision and wall conditions as lbm_adjoint_step.
+ * *out_index = 0 if lam_0 ends in lam_a, 1 if in lam_b.  The states (device, the context's
+ * storage precision and layout) must not alias lam_a or lam_b.  Same precision and wall conditions as lbm_adjoint_step.
  * Asynchronous.                                                                         */
-int lbm_adjoint_chain(lbm_ctx *c, const double *const *states, int n, double *lam_a, double *lam_b,
+int lbm_adjoint_chain(lbm_ctx *c, const void *const *states, int n, void *lam_a, void *lam_b,
                       int *out_index);
 
 /* The adjoint of a step needs f_t only through the fixed-point moments (rho, J = sum c g,
@@ -243,23 +243,23 @@ int lbm_record_moments(lbm_ctx *c, const double *f0, int n, double *work_a, doub
 int lbm_adjoint_chain_moments(lbm_ctx *c, const int64_t *const *moments, int n, double *lam_a,
                               double *lam_b, int *out_index);
 
-/* Adjoint of the width readout (FP64 storage): lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l
- * with dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device, FP64 layout).
- * dL_dTbar is a host array of Lz doubles.  lam_out: device, 37*Lx*Lz doubles.
- * Synchronises.                                                                       */
-int lbm_loss_adjoint(lbm_ctx *c, const double *f, const double *dL_dTbar, double *lam_out);
+/* Adjoint of the width readout: lam(l,x,z) = dL_dTbar[z] / Lx * dT(x,z)/df_l with
+ * dT/df_l = (|xi_l - u|^2 - D T) / (D rho) at the state f (device).  f and lam_out: 37*Lx*Lz
+ * populations in the context's storage precision (FP64 arithmetic); dL_dTbar is a host array
+ * of Lz doubles.  Synchronises.                                                          */
+int lbm_loss_adjoint(lbm_ctx *c, const void *f, const double *dL_dTbar, void *lam_out);
 
-/* Adjoint of lbm_init_layers with respect to the mode amplitudes (FP64 storage): given
- * lam0 = dL/df_0 (device, FP64 layout) returns dL/damp_lo[k] and dL/damp_hi[k] in the
- * host arrays dA_lo, dA_hi (n_modes each).  Synchronises.                             */
-int lbm_init_adjoint(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,
+/* Adjoint of lbm_init_layers with respect to the mode amplitudes: given lam0 = dL/df_0
+ * (device, the context's storage precision and layout) returns dL/damp_lo[k] and
+ * dL/damp_hi[k] in the host arrays dA_lo, dA_hi (n_modes each).  Synchronises.          */
+int lbm_init_adjoint(lbm_ctx *c, const lbm_layers_desc *d, const void *lam0,
                      double *dA_lo, double *dA_hi);
 
 /* lbm_init_adjoint plus, when dph_lo and dph_hi are given (both or neither), the gradient with
  * respect to the mode phases: the interfaces z(x) = z0 + sum_k A_k cos(2 pi k x / Lx + phi_k)
  * (Sec. I) give dL/dphi_k = -A_k sum_x dL/dz(x) sin(2 pi k x / Lx + phi_k).  Host arrays of
  * n_modes doubles.  Synchronises.                                                         */
-int lbm_init_adjoint_full(lbm_ctx *c, const lbm_layers_desc *d, const double *lam0,
+int lbm_init_adjoint_full(lbm_ctx *c, const lbm_layers_desc *d, const void *lam0,
                           double *dA_lo, double *dA_hi, double *dph_lo, double *dph_hi);
 
 /* Wait for all work queued by this context; reports deferred kernel-side errors.     */

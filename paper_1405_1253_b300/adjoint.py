@@ -39,8 +39,9 @@ class AdjointStats:
 
 
 class WidthGradient:
-    """Forward/backward driver for one lattice description on an FP64-storage context:
-    prec "f64_ff" (float-float step and adjoint, the default) or "f64" (native FP64).
+    """Forward/backward driver for one lattice description: prec "f64_ff" (float-float step
+    and adjoint, the default), "f64" (native FP64) or "f32" (FP32 storage and arithmetic:
+    the gradient of the FP32 run, to FP32 rounding).
     store "moments" (f64_ff only, its default): the backward recomputes each segment keeping
     only the per-site moments the adjoint needs (32 bytes per site and step); "states": it
     keeps the segment's states (296 bytes per site and step).  walls=(T_bottom, T_top):
@@ -55,8 +56,8 @@ class WidthGradient:
         self.lat = lat
         self.N = int(nsteps)
         self.K = int(ckpt)
-        if prec not in ("f64", "f64_ff"):
-            raise ValueError("the adjoint needs FP64 storage (prec 'f64' or 'f64_ff')")
+        if prec not in ("f64", "f64_ff", "f32"):
+            raise ValueError("prec is 'f64_ff', 'f64' or 'f32'")
         self.prec = prec
         self.store = store or ("moments" if prec == "f64_ff" and walls is None else "states")
         if self.store not in ("moments", "states") or (self.store == "moments" and (prec != "f64_ff" or walls)):
@@ -66,19 +67,21 @@ class WidthGradient:
             self.L.set_walls(True, *walls)
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
-        self.ckpts = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(self.N // self.K)]
+        dt = self.L.current().dtype              # checkpoints in the storage precision
+        self.ckpts = [torch.empty(n, dtype=dt, device=dev) for _ in range(self.N // self.K)]
         if self.store == "states":
             # states f_{sK+1} .. f_{sK+K-1} of a segment (f_{sK} is its checkpoint)
-            self.seg = torch.empty((self.K - 1, n), dtype=torch.float64, device=dev)
-            seg_bytes = 8 * n * (self.K - 1)
+            self.seg = torch.empty((self.K - 1, n), dtype=dt, device=dev)
+            seg_bytes = self.seg.element_size() * n * (self.K - 1)
         else:
             # moments of the K steps of a segment, and two states to step through
             self.moms = torch.empty((self.K, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
             self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
             seg_bytes = self.moms.numel() * 8 + 2 * 8 * n
-        self.lam = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
-        self.stats = AdjointStats(checkpoint_bytes=8 * n * len(self.ckpts), segment_bytes=seg_bytes,
-                                  state_bytes=8 * n)
+        self.lam = [torch.empty(n, dtype=dt, device=dev) for _ in range(2)]
+        es = self.ckpts[0].element_size() if self.ckpts else 8
+        self.stats = AdjointStats(checkpoint_bytes=es * n * len(self.ckpts), segment_bytes=seg_bytes,
+                                  state_bytes=es * n)
         self._amps = None
 
     def _init(self, amp_lo, amp_hi, ph_lo, ph_hi):
@@ -100,14 +103,14 @@ class WidthGradient:
         t0 = time.perf_counter()
         self._init(amp_lo, amp_hi, ph_lo, ph_hi)
         for s in range(self.N // self.K):
-            self.L.populations_device(self.ckpts[s])
+            self.ckpts[s].copy_(self.L.current())
             self.L.step(self.K)
         widths, dL = self.L.widths(lat.T_u, lat.T_m, lat.T_d, with_grad=True)
         self.stats.forward_s = time.perf_counter() - t0
         self.stats.widths = widths
         self._amps = (amp_lo, amp_hi, ph_lo, ph_hi)
         self._dL = dL
-        self._fN = self.L.populations_device()
+        self._fN = self.L.current().clone()
         return float(widths.sum())
 
     def backward(self, grad_out: float = 1.0):

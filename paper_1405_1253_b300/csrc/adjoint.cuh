@@ -45,113 +45,137 @@ __device__ __forceinline__ PDerivs hermite_poly(double s, double C2, double u2, 
 //   C = rho sum w [ ls (H0 + q (C2-6)/4) + ld s (C2-4)/2 ],
 // and mu_m = (1 - w) lam_m + w (A' + B'.xi_m + C' |xi_m|^2) with
 //   A' = A - B.u/rho + C (|u|^2 - D T)/(D rho),  B' = B/rho - 2 C u/(D rho),  C' = C/(D rho).
+// Lattice constants in the kernel's arithmetic type.
+template <class T>
+struct AdjConst;
+template <>
+struct AdjConst<double> {
+    __device__ static double r() { return d_lat.r; }
+    __device__ static double r2() { return d_lat.r2; }
+    __device__ static double w(int s) { return d_lat.w[s]; }
+};
+template <>
+struct AdjConst<float> {
+    __device__ static float r() { return d_lat.r_hi; }
+    __device__ static float r2() { return d_lat.r2_hi; }
+    __device__ static float w(int s) { return d_lat.wf[s]; }
+};
+
+// T = double: the native FP64 adjoint (LBM_F64 contexts); T = float: FP32 storage and
+// arithmetic (LBM_F32 contexts; accurate to FP32 rounding of the moments and the sums).
+template <class T>
 __global__ void __launch_bounds__(BLOCK_Z)
-k_adjoint_f64(const double* __restrict__ ft, const double* __restrict__ lam_next,
-              double* __restrict__ lam_out, StepParams p) {
+k_adjoint_native(const T* __restrict__ ft, const T* __restrict__ lam_next, T* __restrict__ lam_out,
+                 StepParams p) {
+    using C = AdjConst<T>;
     const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
     const int x = blockIdx.y;
     if (z >= p.Lz) return;
     int col[7];
 #pragma unroll
     for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
-    double g[Q];
+    T g[Q];
     const int n = Q * p.plane;
     static_for<Q>([&](auto l) { g[l.value] = ft[LBM_IDX(pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane), n)]; });
-    const double r = d_lat.r, r2 = d_lat.r2;
-    double R = g[0], Jx = 0.0, Jz = 0.0, E = 0.0;
+    const T r = C::r(), r2 = C::r2();
+    T R = g[0], Jx = T(0), Jz = T(0), E = T(0);
     static_for<NPAIR>([&](auto k) {
         constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
-        const double ps = g[A_] + g[B_], ms = g[A_] - g[B_];
+        const T ps = g[A_] + g[B_], ms = g[A_] - g[B_];
         R += ps;
-        if constexpr (cx(A_) != 0) Jx = fma((double)cx(A_), ms, Jx);
-        if constexpr (cz(A_) != 0) Jz = fma((double)cz(A_), ms, Jz);
-        E = fma((double)c2(A_), ps, E);
+        if constexpr (cx(A_) != 0) Jx = fma(T(cx(A_)), ms, Jx);
+        if constexpr (cz(A_) != 0) Jz = fma(T(cz(A_)), ms, Jz);
+        E = fma(T(c2(A_)), ps, E);
     });
-    const double inv = 1.0 / R;
-    const double ux = r * Jx * inv, uz = r * Jz * inv;
-    const double uu = ux * ux + uz * uz;
-    const double T = 0.5 * (r2 * E * inv - uu);
-    const double usx = ux, usz = uz + p.us_z, th = T + p.T_shift - 1.0;
-    const double u2 = usx * usx + usz * usz;
-    const double a = r * usx, b = r * usz;          // s_l = c_x a + c_z b
+    const T inv = T(1) / R;
+    const T ux = r * Jx * inv, uz = r * Jz * inv;
+    const T uu = ux * ux + uz * uz;
+    const T T_ = T(0.5) * (r2 * E * inv - uu);
+    const T usx = ux, usz = uz + T(p.us_z), th = T_ + T(p.T_shift) - T(1);
+    const T u2 = usx * usx + usz * usz;
+    const T a = r * usx, b = r * usz;          // s_l = c_x a + c_z b
     const int o = x * p.Lz + z;
-    const double lam0 = lam_next[LBM_IDX(o, n)];
+    const T lam0 = lam_next[LBM_IDX(o, n)];
     // rest population (s = 0, C2 = 0)
-    double A = d_lat.w[0] * lam0 * (1.0 - 0.5 * u2 - th + 0.125 * u2 * u2 + th * u2 + th * th);
-    double Bx = 0.0, Bz = 0.0, Bu = d_lat.w[0] * lam0 * (-0.5 + 0.25 * u2 + th);
-    double Cs = d_lat.w[0] * lam0 * (-1.0 + u2 + 2.0 * th);
+    T A = C::w(0) * lam0 * (T(1) - T(0.5) * u2 - th + T(0.125) * u2 * u2 + th * u2 + th * th);
+    T Bx = T(0), Bz = T(0), Bu = C::w(0) * lam0 * (T(-0.5) + T(0.25) * u2 + th);
+    T Cs = C::w(0) * lam0 * (T(-1) + u2 + T(2) * th);
     static_for<NPAIR>([&](auto k) {
         constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
         constexpr int SH = shell_of(A_);
-        const double C2 = r2 * c2(A_);
-        const double K0 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 2.0) + 0.125 * u2 * u2
-                        - 0.25 * th * u2 * (C2 - 4.0) + 0.125 * th * th * (C2 * C2 - 8.0 * C2 + 8.0);
-        const double K1 = 1.0 - 0.5 * u2 + 0.5 * th * (C2 - 4.0);
-        const double K2 = 0.5 - 0.25 * u2 + 0.25 * th * (C2 - 6.0);
-        double s;
-        if constexpr (cx(A_) == 0) s = (double)cz(A_) * b;
-        else if constexpr (cz(A_) == 0) s = (double)cx(A_) * a;
-        else s = fma((double)cx(A_), a, (double)cz(A_) * b);
-        const double q = s * s;
-        const double Ev = fma(q, fma(q, 1.0 / 24.0, K2), K0);
-        const double Od = s * fma(q, 1.0 / 6.0, K1);
-        const double E1 = fma(q, 0.5, K1);
-        const double O1 = s * fma(q, 1.0 / 6.0, 2.0 * K2);
-        const double G0 = -0.5 + 0.25 * u2 - 0.25 * th * (C2 - 4.0);
-        const double H0 = 0.5 * (C2 - 2.0) - 0.25 * u2 * (C2 - 4.0) + 0.25 * th * (C2 * C2 - 8.0 * C2 + 8.0);
-        const double la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
-        const double w = d_lat.w[SH];
-        const double ls = w * (la + lb), ld = w * (la - lb);
+        const T C2 = r2 * T(c2(A_));
+        const T K0 = T(1) - T(0.5) * u2 + T(0.5) * th * (C2 - T(2)) + T(0.125) * u2 * u2
+                   - T(0.25) * th * u2 * (C2 - T(4)) + T(0.125) * th * th * (C2 * C2 - T(8) * C2 + T(8));
+        const T K1 = T(1) - T(0.5) * u2 + T(0.5) * th * (C2 - T(4));
+        const T K2 = T(0.5) - T(0.25) * u2 + T(0.25) * th * (C2 - T(6));
+        T s;
+        if constexpr (cx(A_) == 0) s = T(cz(A_)) * b;
+        else if constexpr (cz(A_) == 0) s = T(cx(A_)) * a;
+        else s = fma(T(cx(A_)), a, T(cz(A_)) * b);
+        const T q = s * s;
+        const T Ev = fma(q, fma(q, T(1.0 / 24.0), K2), K0);
+        const T Od = s * fma(q, T(1.0 / 6.0), K1);
+        const T E1 = fma(q, T(0.5), K1);
+        const T O1 = s * fma(q, T(1.0 / 6.0), T(2) * K2);
+        const T G0 = T(-0.5) + T(0.25) * u2 - T(0.25) * th * (C2 - T(4));
+        const T H0 = T(0.5) * (C2 - T(2)) - T(0.25) * u2 * (C2 - T(4)) + T(0.25) * th * (C2 * C2 - T(8) * C2 + T(8));
+        const T la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
+        const T w = C::w(SH);
+        const T ls = w * (la + lb), ld = w * (la - lb);
         A = fma(ls, Ev, fma(ld, Od, A));
-        const double bt = fma(ld, E1, ls * O1);          // coefficient of xi_A
-        Bx = fma(r * cx(A_), bt, Bx);
-        Bz = fma(r * cz(A_), bt, Bz);
-        Bu = fma(ls, fma(q, -0.25, G0), fma(ld, -0.5 * s, Bu));
-        Cs = fma(ls, fma(0.25 * (C2 - 6.0), q, H0), fma(ld, 0.5 * (C2 - 4.0) * s, Cs));
+        const T bt = fma(ld, E1, ls * O1);          // coefficient of xi_A
+        Bx = fma(r * T(cx(A_)), bt, Bx);
+        Bz = fma(r * T(cz(A_)), bt, Bz);
+        Bu = fma(ls, fma(q, T(-0.25), G0), fma(ld, T(-0.5) * s, Bu));
+        Cs = fma(ls, fma(T(0.25) * (C2 - T(6)), q, H0), fma(ld, T(0.5) * (C2 - T(4)) * s, Cs));
     });
     // dP/du_s = dP/ds xi + 2 dP/du2 u_s, times rho
-    const double Bxt = R * (Bx + 2.0 * Bu * usx);
-    const double Bzt = R * (Bz + 2.0 * Bu * usz);
-    const double Ct = R * Cs;
-    const double Dr = DIM * R;
-    const double Ap = A - (Bxt * ux + Bzt * uz) * inv + Ct * (uu - DIM * T) / Dr;
-    const double Bpx = Bxt * inv - 2.0 * Ct * ux / Dr;
-    const double Bpz = Bzt * inv - 2.0 * Ct * uz / Dr;
-    const double Cp = Ct / Dr;
+    const T Bxt = R * (Bx + T(2) * Bu * usx);
+    const T Bzt = R * (Bz + T(2) * Bu * usz);
+    const T Ct = R * Cs;
+    const T Dr = T(DIM) * R;
+    const T Ap = A - (Bxt * ux + Bzt * uz) * inv + Ct * (uu - T(DIM) * T_) / Dr;
+    const T Bpx = Bxt * inv - T(2) * Ct * ux / Dr;
+    const T Bpz = Bzt * inv - T(2) * Ct * uz / Dr;
+    const T Cp = Ct / Dr;
+    const T om = T(p.omega), omo = T(p.one_m_omega);
     // scatter mu to the pull sources (unique targets: propagate + bc is a permutation)
-    lam_out[LBM_IDX(pull_index<0>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, lam0, p.omega * Ap);
+    lam_out[LBM_IDX(pull_index<0>(x, z, col, p.Lz, p.plane), n)] = fma(omo, lam0, om * Ap);
     static_for<NPAIR>([&](auto k) {
         constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
-        const double ev = fma(Cp, r2 * c2(A_), Ap);
-        const double od = fma(Bpx, r * cx(A_), Bpz * (r * cz(A_)));
-        const double la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
-        lam_out[LBM_IDX(pull_index<A_>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, la, p.omega * (ev + od));
-        lam_out[LBM_IDX(pull_index<B_>(x, z, col, p.Lz, p.plane), n)] = fma(p.one_m_omega, lb, p.omega * (ev - od));
+        const T ev = fma(Cp, r2 * T(c2(A_)), Ap);
+        const T od = fma(Bpx, r * T(cx(A_)), Bpz * (r * T(cz(A_))));
+        const T la = lam_next[LBM_IDX(A_ * p.plane + o, n)], lb = lam_next[LBM_IDX(B_ * p.plane + o, n)];
+        lam_out[LBM_IDX(pull_index<A_>(x, z, col, p.Lz, p.plane), n)] = fma(omo, la, om * (ev + od));
+        lam_out[LBM_IDX(pull_index<B_>(x, z, col, p.Lz, p.plane), n)] = fma(omo, lb, om * (ev - od));
     });
 }
 
-// lam_N(l,x,z) = dL[z] / Lx * (|xi_l - u|^2 - D T)/(D rho) at the stored state f.
-__global__ void k_loss_adjoint(const double* __restrict__ f, const double* __restrict__ dL,
-                               double* __restrict__ lam, int Lx, int Lz) {
+// lam_N(l,x,z) = dL[z] / Lx * (|xi_l - u|^2 - D T)/(D rho) at the stored state f (storage
+// policy S: FP64 or FP32 populations and adjoint; the arithmetic is FP64).
+template <class S>
+__global__ void k_loss_adjoint(const typename S::T* __restrict__ f, const double* __restrict__ dL,
+                               typename S::T* __restrict__ lam, int Lx, int Lz) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int x = blockIdx.y;
     if (z >= Lz) return;
     double R, ux, uz, T;
-    site_moments<StoreF64>(f, x, z, Lz, Lx * Lz, R, ux, uz, T);
+    site_moments<S>(f, x, z, Lz, Lx * Lz, R, ux, uz, T);
     const double scale = dL[z] / (double)Lx / (DIM * R);
     const int o = x * Lz + z;
 #pragma unroll
     for (int l = 0; l < Q; l++) {
         const double dx = d_lat.r * cx(l) - ux, dz = d_lat.r * cz(l) - uz;
-        lam[l * Lx * Lz + o] = scale * (dx * dx + dz * dz - DIM * T);
+        S::put(lam, l * Lx * Lz + o, scale * (dx * dx + dz * dz - DIM * T));
     }
 }
 
 // Per column x: sum_{z,l} lam0 df0/dz_lo(x) -> colred[x], same for z_hi -> colred[Lx + x].
 // f0 = f^eq(rho, (0, -g/2), T), rho = p/T with p and T as in layer_p_T; p is continuous
 // across the interfaces, so moving an interface adds no boundary term.
+template <class S>
 __global__ void __launch_bounds__(128)
-k_init_adjoint_columns(const double* __restrict__ lam0, const double* __restrict__ zc, InitParams ip,
+k_init_adjoint_columns(const typename S::T* __restrict__ lam0, const double* __restrict__ zc, InitParams ip,
                        double* __restrict__ colred) {
     __shared__ double sm[2][128];
     const int x = blockIdx.x;
@@ -176,7 +200,7 @@ k_init_adjoint_columns(const double* __restrict__ lam0, const double* __restrict
         for (int l = 0; l < Q; l++) {
             const double s = d_lat.r * cz(l) * uz;
             const PDerivs d = hermite_poly(s, d_lat.r2 * c2(l), u2, th);
-            const double lv = lam0[l * ip.plane + x * ip.Lz + k];
+            const double lv = S::get(lam0, l * ip.plane + x * ip.Lz + k);
             const double w = d_lat.w[shell_of(l)];
             s_feq_rho += lv * w * d.P;           // f^eq / rho
             s_dfdT += lv * w * rho * d.dPdth;    // df^eq / dT

@@ -830,16 +830,21 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
 // ---------------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------------
-static void launch_adjoint(const lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out,
+// Buffers in the context's storage precision (double for LBM_F64 / LBM_F64_FF, float for LBM_F32).
+static void launch_adjoint(const lbm_ctx* c, const void* f_t, const void* lam_next, void* lam_out,
                            const StepParams& p) {
+    const double *fd = (const double*)f_t, *ld = (const double*)lam_next;
+    double* od = (double*)lam_out;
+    dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
     if (c->thermal) {               // LBM_F64_FF with its ghost scratch (adjoint_walls_ready)
-        launch_adjoint_ff_thermal(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, c->tw, c->gmu, c->stream);
+        launch_adjoint_ff_thermal(fd, ld, od, p, quad_w_shell(), g_quad.r, c->tw, c->gmu, c->stream);
     } else if (c->prec == LBM_F64_FF) {
-        launch_adjoint_ff(f_t, lam_next, lam_out, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z),
-                          c->stream);
+        launch_adjoint_ff(fd, ld, od, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z), c->stream);
+    } else if (c->prec == LBM_F64) {
+        k_adjoint_native<double><<<grid, BLOCK_Z, 0, c->stream>>>(fd, ld, od, p);
     } else {
-        dim3 grid((c->Lz + BLOCK_Z - 1) / BLOCK_Z, c->Lx);
-        k_adjoint_f64<<<grid, BLOCK_Z, 0, c->stream>>>(f_t, lam_next, lam_out, p);
+        k_adjoint_native<float><<<grid, BLOCK_Z, 0, c->stream>>>((const float*)f_t, (const float*)lam_next,
+                                                                 (float*)lam_out, p);
     }
 }
 
@@ -853,9 +858,8 @@ static int adjoint_walls_ready(lbm_ctx* c) {
     return LBM_OK;
 }
 
-int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, double* lam_out) {
+int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const void* lam_next, void* lam_out) {
     if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
     DeviceGuard dg(c->device);
     int rc = adjoint_walls_ready(c);
@@ -865,10 +869,9 @@ int lbm_adjoint_step(lbm_ctx* c, const double* f_t, const double* lam_next, doub
     return LBM_OK;
 }
 
-int lbm_adjoint_chain(lbm_ctx* c, const double* const* states, int n, double* lam_a, double* lam_b, int* out_index) {
+int lbm_adjoint_chain(lbm_ctx* c, const void* const* states, int n, void* lam_a, void* lam_b, int* out_index) {
     if (!c || !states || !lam_a || !lam_b || !out_index) return fail(LBM_EINVAL, "NULL argument");
     if (n < 0) return fail(LBM_EINVAL, "n < 0");
-    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     if (lam_a == lam_b) return fail(LBM_EINVAL, "lam_a and lam_b must differ");
     for (int j = 0; j < n; j++) {
         if (!states[j]) return fail(LBM_EINVAL, "state %d is NULL", j);
@@ -878,7 +881,7 @@ int lbm_adjoint_chain(lbm_ctx* c, const double* const* states, int n, double* la
     int rc = adjoint_walls_ready(c);
     if (rc) return rc;
     const StepParams p = step_params(c);
-    double* lam[2] = {lam_a, lam_b};
+    void* lam[2] = {lam_a, lam_b};
     int cur = 0;
     for (int j = n - 1; j >= 0; j--) {
         launch_adjoint(c, states[j], lam[cur], lam[cur ^ 1], p);
@@ -934,22 +937,24 @@ int lbm_adjoint_chain_moments(lbm_ctx* c, const int64_t* const* moments, int n, 
     return LBM_OK;
 }
 
-int lbm_loss_adjoint(lbm_ctx* c, const double* f, const double* dL_dTbar, double* lam_out) {
+int lbm_loss_adjoint(lbm_ctx* c, const void* f, const double* dL_dTbar, void* lam_out) {
     if (!c || !f || !dL_dTbar || !lam_out) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     DeviceGuard dg(c->device);
     CU(cudaMemcpyAsync(c->dLrow, dL_dTbar, (size_t)c->Lz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     dim3 grid((c->Lz + 127) / 128, c->Lx);
-    k_loss_adjoint<<<grid, 128, 0, c->stream>>>(f, c->dLrow, lam_out, c->Lx, c->Lz);
+    if (c->prec == LBM_F32)
+        k_loss_adjoint<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, c->dLrow, (float*)lam_out, c->Lx, c->Lz);
+    else
+        k_loss_adjoint<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->dLrow, (double*)lam_out, c->Lx,
+                                                              c->Lz);
     LAUNCH_CHECK();
     CU(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
-int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi,
+int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const void* lam0, double* dA_lo, double* dA_hi,
                           double* dph_lo, double* dph_hi) {
     if (!c || !lam0) return fail(LBM_EINVAL, "NULL argument");
-    if (c->prec == LBM_F32) return fail(LBM_ESTATE, "the adjoint needs FP64 storage (LBM_F64 or LBM_F64_FF)");
     DeviceGuard dg(c->device);
     InitParams ip;
     int rc = fill_init_params(c, d, &ip);
@@ -958,7 +963,10 @@ int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const double* la
     if ((dph_lo == nullptr) != (dph_hi == nullptr)) return fail(LBM_EINVAL, "give both phase outputs or neither");
     k_interfaces<<<(c->Lx + 127) / 128, 128, 0, c->stream>>>(c->zcol, c->modes, ip);
     LAUNCH_CHECK();
-    k_init_adjoint_columns<<<c->Lx, 128, 0, c->stream>>>(lam0, c->zcol, ip, c->colred);
+    if (c->prec == LBM_F32)
+        k_init_adjoint_columns<StoreF32><<<c->Lx, 128, 0, c->stream>>>((const float*)lam0, c->zcol, ip, c->colred);
+    else
+        k_init_adjoint_columns<StoreF64><<<c->Lx, 128, 0, c->stream>>>((const double*)lam0, c->zcol, ip, c->colred);
     LAUNCH_CHECK();
     if (d->n_modes == 0) return lbm_sync(c);
     const int K = d->n_modes;
@@ -980,7 +988,7 @@ int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const double* la
     return LBM_OK;
 }
 
-int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const double* lam0, double* dA_lo, double* dA_hi) {
+int lbm_init_adjoint(lbm_ctx* c, const lbm_layers_desc* d, const void* lam0, double* dA_lo, double* dA_hi) {
     return lbm_init_adjoint_full(c, d, lam0, dA_lo, dA_hi, nullptr, nullptr);
 }
 

@@ -129,3 +129,17 @@ def test_phase_gradient_matches_oracle_chain_and_finite_differences(adj):
         assert abs(fd_lo - p_lo[k]) < 1e-4 * max(1.0, abs(fd_lo))
         assert abs(fd_hi - p_hi[k]) < 1e-4 * max(1.0, abs(fd_hi))
     drv.close()
+
+
+def test_fp32_gradient_tracks_fp64_gradient(adj):
+    """The gradient of an FP32-storage run (FP32 forward, FP32 adjoint) against the
+    float-float gradient of the same problem: the same to FP32-level accuracy."""
+    lat = W.Lattice(64, 192, tau=0.8, grav=1e-4, K=4, sigma=1.0, seed=22)
+    m = lat.modes()
+    g = {}
+    for prec in ("f32", "f64_ff"):
+        drv = adj.WidthGradient(lat, 200, 20, prec=prec)
+        drv.forward(m.amp_lo, m.amp_hi)
+        g[prec] = np.concatenate(drv.backward())
+        drv.close()
+    assert np.linalg.norm(g["f32"] - g["f64_ff"]) / np.linalg.norm(g["f64_ff"]) < 1e-3
