@@ -64,9 +64,8 @@ struct AdjConst<float> {
 // T = double: the native FP64 adjoint (LBM_F64 contexts); T = float: FP32 storage and
 // arithmetic (LBM_F32 contexts; accurate to FP32 rounding of the moments and the sums).
 template <class T>
-__global__ void __launch_bounds__(BLOCK_Z)
-k_adjoint_native(const T* __restrict__ ft, const T* __restrict__ lam_next, T* __restrict__ lam_out,
-                 StepParams p) {
+__device__ __forceinline__ void adjoint_native_site(const T* __restrict__ ft, const T* __restrict__ lam_next,
+                                                    T* __restrict__ lam_out, const StepParams& p) {
     using C = AdjConst<T>;
     const int z = blockIdx.x * BLOCK_Z + threadIdx.x;
     const int x = blockIdx.y;
@@ -149,6 +148,21 @@ k_adjoint_native(const T* __restrict__ ft, const T* __restrict__ lam_next, T* __
         lam_out[LBM_IDX(pull_index<A_>(x, z, col, p.Lz, p.plane), n)] = fma(omo, la, om * (ev + od));
         lam_out[LBM_IDX(pull_index<B_>(x, z, col, p.Lz, p.plane), n)] = fma(omo, lb, om * (ev - od));
     });
+}
+
+__global__ void __launch_bounds__(BLOCK_Z)
+k_adjoint_native_f64(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
+                     StepParams p) {
+    adjoint_native_site(ft, lam_next, lam_out, p);
+}
+
+// The FP32 form is held by memory latency: 7 resident blocks per SM (72 registers, a small
+// spill) instead of the 4 its unconstrained 118 registers allow (measured: 4 blocks 0.253 ms,
+// 6 blocks 0.203, 7 and 8 blocks 0.187 on 1024 x 2048).
+__global__ void __launch_bounds__(BLOCK_Z, 7)
+k_adjoint_native_f32(const float* __restrict__ ft, const float* __restrict__ lam_next, float* __restrict__ lam_out,
+                     StepParams p) {
+    adjoint_native_site(ft, lam_next, lam_out, p);
 }
 
 // lam_N(l,x,z) = dL[z] / Lx * (|xi_l - u|^2 - D T)/(D rho) at the stored state f (storage
