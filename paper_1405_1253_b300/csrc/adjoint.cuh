@@ -74,7 +74,7 @@ __device__ __forceinline__ void adjoint_native_site(const T* __restrict__ ft, co
 #pragma unroll
     for (int k = 0; k < 7; k++) col[k] = wrap_x(x + k - 3, p.Lx) * p.Lz;
     T g[Q];
-    const int n = Q * p.plane;
+    [[maybe_unused]] const int n = Q * p.plane;      // element count for bounds-checked builds
     static_for<Q>([&](auto l) { g[l.value] = ft[LBM_IDX(pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane), n)]; });
     const T r = C::r(), r2 = C::r2();
     T R = g[0], Jx = T(0), Jz = T(0), E = T(0);

@@ -32,7 +32,7 @@ struct DstSourceThermal {
     const SiteAddr& ad;
     __device__ __forceinline__ void one(int l, int vx, int vz, double v) const {
         const int zs = ad.z - vz;
-        const int ng = 6 * Q * ad.Lx;
+        [[maybe_unused]] const int ng = 6 * Q * ad.Lx;     // element count for bounds-checked builds
         if (zs < 0) {
             gmu[LBM_IDX(ghost_mu_index(0, l, ad.x, ad.z, ad.Lx), ng)] = v;
         } else if (zs >= ad.Lz) {
@@ -77,7 +77,7 @@ k_adjoint_thermal_ghosts(double* __restrict__ lam_out, const double* __restrict_
     if (i >= 2 * Lx) return;
     const int top = i >= Lx;
     const int xg = top ? i - Lx : i;
-    const int ng = 6 * Q * Lx;
+    [[maybe_unused]] const int ng = 6 * Q * Lx;
     double om = 0.0;
     // destinations that pull from this ghost column: column xg + c_x, rows whose source lies
     // beyond the wall (bottom: z < c_z; top: z >= Lz + c_z, row r = z - (Lz - 3))

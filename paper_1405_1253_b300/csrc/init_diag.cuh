@@ -365,7 +365,7 @@ k_propagate(const T* __restrict__ fin, T* __restrict__ fout, int Lx, int Lz, Til
     bool wall;
     if (!ad.setup(Lx, Lz, Lx * Lz, t, blockIdx.x, wall)) return;
     const int o = ad.dst();
-    const int n = Q * ad.plane;
+    [[maybe_unused]] const int n = Q * ad.plane;     // element count for bounds-checked builds
     if (wall) static_for<Q>([&](auto l) {
         fout[LBM_IDX(l.value * ad.plane + o, n)] = fin[LBM_IDX((ad.template src<decltype(l)::value, true>()), n)];
     });

@@ -85,45 +85,56 @@ struct Quadrature {
     int ok;
 };
 
+// Host helpers of the quadrature solve (plain functions: a lambda would also be compiled for
+// the device, where long double is not available).
+// Moment of order a of the unit Gaussian: (a - 1)!! for even a, 0 for odd a.
+inline long double quad_gauss_moment(int a) {
+    if (a % 2) return 0.0L;
+    long double m = 1.0L;
+    for (int k = a - 1; k > 0; k -= 2) m *= k;
+    return m;
+}
+inline long double quad_ipow(long double b, int e) {
+    long double p = 1.0L;
+    for (int i = 0; i < e; i++) p *= b;
+    return p;
+}
+// The nine moment exponents (e_x, e_z) the quadrature must reproduce.
+constexpr int QUAD_E[9][2] = {{0, 0}, {2, 0}, {4, 0}, {2, 2}, {6, 0}, {4, 2}, {8, 0}, {6, 2}, {4, 4}};
+// A[e][s](r) = sum over shell s of xi_x^ex xi_z^ez, dA/dr and the Gaussian moments rhs[e].
+inline void quad_system(long double r, long double A[9][NSHELL], long double dA[9][NSHELL], long double rhs[9]) {
+    for (int e = 0; e < 9; e++) {
+        rhs[e] = quad_gauss_moment(QUAD_E[e][0]) * quad_gauss_moment(QUAD_E[e][1]);
+        for (int s = 0; s < NSHELL; s++) { A[e][s] = 0; dA[e][s] = 0; }
+        const int deg = QUAD_E[e][0] + QUAD_E[e][1];
+        for (int l = 0; l < Q; l++) {
+            const long double mono = quad_ipow((long double)cx(l), QUAD_E[e][0]) * quad_ipow((long double)cz(l), QUAD_E[e][1]);
+            A[e][shell_of(l)] += mono * quad_ipow(r, deg);
+            if (deg > 0) dA[e][shell_of(l)] += mono * deg * quad_ipow(r, deg - 1);
+        }
+    }
+}
+// Gauss-Jordan with partial pivoting on an n x (n+1) augmented matrix; false if singular.
+inline bool quad_solve(int n, long double M[9][10]) {
+    for (int c = 0; c < n; c++) {
+        int p = c;
+        for (int i = c + 1; i < n; i++) if (fabsl(M[i][c]) > fabsl(M[p][c])) p = i;
+        if (M[p][c] == 0) return false;
+        for (int j = 0; j <= n; j++) { const long double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
+        for (int i = 0; i < n; i++) {
+            if (i == c) continue;
+            const long double f = M[i][c] / M[c][c];
+            for (int j = c; j <= n; j++) M[i][j] -= f * M[c][j];
+        }
+    }
+    for (int i = 0; i < n; i++) M[i][n] /= M[i][i];
+    return true;
+}
+
 inline Quadrature solve_quadrature_host() {
     typedef long double ld;
-    const int E[9][2] = {{0, 0}, {2, 0}, {4, 0}, {2, 2}, {6, 0}, {4, 2}, {8, 0}, {6, 2}, {4, 4}};
-    auto gm = [](int a) -> ld {
-        if (a % 2) return 0.0L;
-        ld m = 1.0L;
-        for (int k = a - 1; k > 0; k -= 2) m *= k;
-        return m;
-    };
-    auto ipow = [](ld b, int e) -> ld { ld p = 1.0L; for (int i = 0; i < e; i++) p *= b; return p; };
-    // A[e][s](r), dA/dr and the right-hand side
-    auto build = [&](ld r, ld A[9][NSHELL], ld dA[9][NSHELL], ld rhs[9]) {
-        for (int e = 0; e < 9; e++) {
-            rhs[e] = gm(E[e][0]) * gm(E[e][1]);
-            for (int s = 0; s < NSHELL; s++) { A[e][s] = 0; dA[e][s] = 0; }
-            int deg = E[e][0] + E[e][1];
-            for (int l = 0; l < Q; l++) {
-                ld mono = ipow((ld)cx(l), E[e][0]) * ipow((ld)cz(l), E[e][1]);
-                A[e][shell_of(l)] += mono * ipow(r, deg);
-                if (deg > 0) dA[e][shell_of(l)] += mono * deg * ipow(r, deg - 1);
-            }
-        }
-    };
-    // Gauss-Jordan with partial pivoting on an n x (n+1) augmented matrix.
-    auto solve = [](int n, ld M[9][10]) -> bool {
-        for (int c = 0; c < n; c++) {
-            int p = c;
-            for (int i = c + 1; i < n; i++) if (fabsl(M[i][c]) > fabsl(M[p][c])) p = i;
-            if (M[p][c] == 0) return false;
-            for (int j = 0; j <= n; j++) { ld t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
-            for (int i = 0; i < n; i++) {
-                if (i == c) continue;
-                ld f = M[i][c] / M[c][c];
-                for (int j = c; j <= n; j++) M[i][j] -= f * M[c][j];
-            }
-        }
-        for (int i = 0; i < n; i++) M[i][n] /= M[i][i];
-        return true;
-    };
+    const auto build = quad_system;
+    const auto solve = quad_solve;
     Quadrature q{};
     ld r = 1.2L, w[NSHELL];
     ld A[9][NSHELL], dA[9][NSHELL], rhs[9];

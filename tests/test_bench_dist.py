@@ -49,3 +49,31 @@ def test_aggregate_over_two_gloo_ranks():
 def test_single_rank_needs_no_collective():
     import bench
     assert bench.aggregate_ranks(80.0, 40, 2000, 1) == (80.0, 2.0, 2000 / 2e-3 / 1e6)
+
+
+def _reference_line(monkeypatch, capsys, steps, warmup, rank="0"):
+    import argparse
+    import json
+    import bench
+    monkeypatch.setenv("RANK", rank)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 2.0)
+    bench.run_reference(argparse.Namespace(steps=steps, warmup=warmup, gpus=1))
+    out = capsys.readouterr().out.strip()
+    return json.loads(out) if out else None
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The oracle arm prints one line with the contract's keys; its window shrinks to keep a
+    long run within the oracle-time budget."""
+    line = _reference_line(monkeypatch, capsys, steps=3, warmup=1)
+    assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["steps"] == 3 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    long_run = _reference_line(monkeypatch, capsys, steps=100, warmup=3)
+    assert long_run["config"]["sample"].startswith("16x2048")
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
+    assert _reference_line(monkeypatch, capsys, steps=3, warmup=1, rank="1") is None
