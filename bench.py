@@ -271,13 +271,14 @@ def bench_ensemble(torch, lbm, prec, steps, stream):
 
 def bench_adjoint(torch):
     """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and backward
-    (recompute + adjoint) wall times and device memory, for both backward stores of the
-    float-float driver (moment records, segment states) and for an FP32-storage run."""
+    (recompute + adjoint) wall times and device memory, for the three backward stores of the
+    float-float driver (recomputed moment records, moment records taped in the forward,
+    segment states) and for an FP32-storage run."""
     from paper_1405_1253_b300 import adjoint
     lat = W.GRADIENT_256x512
     out = {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (f64_ff)"}
     m = lat.modes()
-    for store, prec in (("moments", "f64_ff"), ("states", "f64_ff"), ("states", "f32")):
+    for store, prec in (("moments", "f64_ff"), ("tape", "f64_ff"), ("states", "f64_ff"), ("states", "f32")):
         key = store if prec == "f64_ff" else "f32"
         drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store)
         drv.forward(m.amp_lo, m.amp_hi)      # warm
@@ -292,6 +293,8 @@ def bench_adjoint(torch):
                       "memory_bytes": mem, "forward_memory_bytes": 2 * st.state_bytes,
                       "memory_over_forward": mem / (2 * st.state_bytes),
                       "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
+    # the tape's forward also writes the moment records: its backward against the plain forward too
+    out["tape"]["backward_over_plain_forward"] = out["tape"]["backward_s"] / out["moments"]["forward_s"]
     return out
 
 def bench_slabs(torch, lbm, lat, steps, stream, prec="f64_ff"):

@@ -11,7 +11,9 @@ adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA l
 this module only orders the calls and owns the buffers (through PyTorch).
 
 Memory: (N/K) checkpoints and 2 adjoint fields, each 37 Lx Lz doubles, and per segment either
-(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through.
+(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through.  The
+"tape" store instead records the moments of all N steps during the forward pass (32 bytes per
+site and step, no checkpoints), so the backward recomputes nothing.
 """
 from __future__ import annotations
 
@@ -44,8 +46,11 @@ class WidthGradient:
     the gradient of the FP32 run, to FP32 rounding).
     store "moments" (f64_ff only, its default): the backward recomputes each segment keeping
     only the per-site moments the adjoint needs (32 bytes per site and step); "states": it
-    keeps the segment's states (296 bytes per site and step).  walls=(T_bottom, T_top):
-    thermal walls (lbm_set_walls) in the forward and the adjoint (f64_ff, states)."""
+    keeps the segment's states (296 bytes per site and step); "tape" (f64_ff only): the
+    forward records the moments of every step (N x 32 bytes per site; ckpt only sets the
+    length of each adjoint chain call) and the backward runs the adjoint steps alone.
+    walls=(T_bottom, T_top): thermal walls (lbm_set_walls) in the forward and the adjoint
+    (f64_ff, states)."""
 
     def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None,
                  walls=None):
@@ -60,16 +65,23 @@ class WidthGradient:
             raise ValueError("prec is 'f64_ff', 'f64' or 'f32'")
         self.prec = prec
         self.store = store or ("moments" if prec == "f64_ff" and walls is None else "states")
-        if self.store not in ("moments", "states") or (self.store == "moments" and (prec != "f64_ff" or walls)):
-            raise ValueError("store is 'states', or 'moments' with prec 'f64_ff' and bounce-back walls")
+        if self.store not in ("moments", "states", "tape") or (
+                self.store != "states" and (prec != "f64_ff" or walls)):
+            raise ValueError("store is 'states', or 'moments' / 'tape' with prec 'f64_ff' and bounce-back walls")
         self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
         if walls is not None:                      # thermal walls at (T_bottom, T_top)
             self.L.set_walls(True, *walls)
         n = Q * lat.Lx * lat.Lz
         dev = self.L.device
         dt = self.L.current().dtype              # checkpoints in the storage precision
-        self.ckpts = [torch.empty(n, dtype=dt, device=dev) for _ in range(self.N // self.K)]
-        if self.store == "states":
+        nck = 0 if self.store == "tape" else self.N // self.K
+        self.ckpts = [torch.empty(n, dtype=dt, device=dev) for _ in range(nck)]
+        if self.store == "tape":
+            # moments of all N steps, and two states to step through
+            self.moms = torch.empty((self.N, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
+            self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+            seg_bytes = self.moms.numel() * 8 + 2 * 8 * n
+        elif self.store == "states":
             # states f_{sK+1} .. f_{sK+K-1} of a segment (f_{sK} is its checkpoint)
             self.seg = torch.empty((self.K - 1, n), dtype=dt, device=dev)
             seg_bytes = self.seg.element_size() * n * (self.K - 1)
@@ -79,7 +91,7 @@ class WidthGradient:
             self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
             seg_bytes = self.moms.numel() * 8 + 2 * 8 * n
         self.lam = [torch.empty(n, dtype=dt, device=dev) for _ in range(2)]
-        es = self.ckpts[0].element_size() if self.ckpts else 8
+        es = self.lam[0].element_size()
         self.stats = AdjointStats(checkpoint_bytes=es * n * len(self.ckpts), segment_bytes=seg_bytes,
                                   state_bytes=es * n)
         self._amps = None
@@ -102,9 +114,14 @@ class WidthGradient:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         self._init(amp_lo, amp_hi, ph_lo, ph_hi)
-        for s in range(self.N // self.K):
-            self.ckpts[s].copy_(self.L.current())
-            self.L.step(self.K)
+        if self.store == "tape":
+            # the N steps, recording each one's moments; f_N ends in work[(N - 1) % 2]
+            self.L.record_moments(self.L.current(), self.work[0], self.work[1], list(self.moms))
+            self.L.current().copy_(self.work[(self.N - 1) % 2])
+        else:
+            for s in range(self.N // self.K):
+                self.ckpts[s].copy_(self.L.current())
+                self.L.step(self.K)
         widths, dL = self.L.widths(lat.T_u, lat.T_m, lat.T_d, with_grad=True)
         self.stats.forward_s = time.perf_counter() - t0
         self.stats.widths = widths
@@ -125,7 +142,10 @@ class WidthGradient:
         cur, nxt = self.lam
         self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
         for s in range(self.N // self.K - 1, -1, -1):
-            if self.store == "states":
+            if self.store == "tape":
+                # the K recorded steps of segment s, adjoint steps only
+                flip = self.L.adjoint_chain_moments([self.moms[s * self.K + j] for j in range(self.K)], cur, nxt)
+            elif self.store == "states":
                 # recompute f_{sK+1} .. f_{sK+K-1} from the checkpoint into the segment buffers
                 # (one library call), then the K adjoint steps of the segment (one call)
                 states = [self.ckpts[s]] + [self.seg[j] for j in range(self.K - 1)]

@@ -16,7 +16,8 @@ def adj():
     return adjoint
 
 
-@pytest.mark.parametrize("prec,store", [("f64", "states"), ("f64_ff", "states"), ("f64_ff", "moments")])
+@pytest.mark.parametrize("prec,store", [("f64", "states"), ("f64_ff", "states"), ("f64_ff", "moments"),
+                                        ("f64_ff", "tape")])
 def test_gradient_matches_oracle_chain(adj, prec, store):
     lat = W.Lattice(12, 48, tau=0.8, grav=1e-3, K=2, sigma=1.0, seed=21)
     nsteps, ckpt = 6, 3
@@ -85,16 +86,32 @@ def test_gradient_vs_finite_differences_256x512_2000_steps(adj):
 
 
 def test_moment_store_gives_the_same_gradient(adj):
-    """The two backward stores of the float-float driver give the same gradient bit for bit."""
+    """The three backward stores of the float-float driver (segment states, recomputed moment
+    records, moment records taped in the forward) give the same loss and the same amplitude
+    and phase gradients bit for bit; the tape recomputes no step."""
     lat = W.Lattice(40, 96, tau=0.8, grav=1e-4, K=3, sigma=1.0, seed=25)
     m = lat.modes()
     out = []
-    for store in ("states", "moments"):
+    for store in ("states", "moments", "tape"):
         drv = adj.WidthGradient(lat, 60, 20, store=store)
-        drv.forward(m.amp_lo, m.amp_hi)
-        out.append(np.concatenate(drv.backward()))
+        val = drv.forward(m.amp_lo, m.amp_hi)
+        g = np.concatenate(drv.backward())
+        out.append((val, g, np.concatenate(drv.grad_phases)))
+        if store == "tape":
+            assert drv.stats.recompute_steps == 0 and drv.stats.adjoint_steps == 60
+            assert drv.stats.checkpoint_bytes == 0
         drv.close()
-    np.testing.assert_array_equal(out[0], out[1])
+    for val, g, gp in out[1:]:
+        assert val == out[0][0]
+        np.testing.assert_array_equal(g, out[0][1])
+        np.testing.assert_array_equal(gp, out[0][2])
+
+
+def test_tape_store_refuses_other_precisions_and_walls(adj):
+    lat = W.Lattice(8, 24, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=26)
+    for kw in ({"prec": "f64"}, {"prec": "f32"}, {"walls": (1.02, 0.98)}):
+        with pytest.raises(ValueError):
+            adj.WidthGradient(lat, 4, 2, store="tape", **kw)
 
 
 def test_phase_gradient_matches_oracle_chain_and_finite_differences(adj):
