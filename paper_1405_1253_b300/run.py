@@ -1,8 +1,9 @@
 """Command-line runner: initialise a three-layer lattice and advance it; optionally apply
-the adjoint step to a seeded random field at the final state (FP64 storage only).
+the adjoint step to a seeded random field at the final state (in the storage precision).
 
   python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3 [--store moments]
+  python -m paper_1405_1253_b300.run --prec f64_ff --steps 3 --walls      (thermal walls)
 
 Used as the profiled program of the ncu summaries under profiles/.
 """
@@ -28,20 +29,24 @@ def main():
     ap.add_argument("--adjoint", type=int, default=0, help="adjoint steps after the forward steps")
     ap.add_argument("--store", default="states", choices=["states", "moments"],
                     help="the adjoint reads the state (gathers f_t) or a moment record of the step")
+    ap.add_argument("--walls", action="store_true", help="thermal walls at the bottom and top layer temperatures")
     args = ap.parse_args()
     from . import lbm
     lat = W.Lattice(args.Lx, args.Lz, tau=args.tau, grav=args.grav, K=args.modes, sigma=args.sigma, seed=args.seed)
     L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=args.prec)
     L.init_from(lat)
+    if args.walls:
+        L.set_walls(True, lat.T_d, lat.T_u)
     L.step(args.steps)
     L.sync()
     mass, energy = L.global_sums()
-    out = {"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "mass": mass, "energy": energy}
+    out = {"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "walls": args.walls,
+           "mass": mass, "energy": energy}
     if args.adjoint > 0:
         import torch
-        f = L.populations_device().clone()
+        f = L.current().clone()                   # the state in the storage precision
         gen = torch.Generator(device=f.device).manual_seed(args.seed)
-        lam = [torch.rand(f.numel(), dtype=torch.float64, device=f.device, generator=gen), torch.empty_like(f)]
+        lam = [torch.rand(f.numel(), dtype=f.dtype, device=f.device, generator=gen), torch.empty_like(f)]
         if args.store == "moments":
             mom = [torch.empty(4 * lat.Lx * lat.Lz, dtype=torch.int64, device=f.device)]
             L.record_moments(f, torch.empty_like(f), torch.empty_like(f), mom)
