@@ -185,4 +185,93 @@ __device__ __forceinline__ double ff_to_double_bits(ff a) {
     return __longlong_as_double((long long)P);
 }
 
+// ---------------------------------------------------------------------------------
+// Two float-float values in the lanes of packed FP32 registers (B300's f32x2 add, sub and
+// mul: one instruction for both lanes).  Each lane takes exactly the operations of the
+// scalar functions above, so results are bit-identical to them.  The FMAs of the error
+// terms stay scalar (two per pair of lanes): a packed FMA takes as long as two scalar ones,
+// and the scalar form negates its addend for free, which the packed one cannot.
+// ---------------------------------------------------------------------------------
+typedef unsigned long long f32x2;       // lane 0 in the low word, lane 1 in the high word
+
+__device__ __forceinline__ f32x2 x2_pack(float l0, float l1) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(l0), "f"(l1));
+    return r;
+}
+__device__ __forceinline__ float x2_lane0(f32x2 v) {
+    float l0, l1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(v));
+    return l0;
+}
+__device__ __forceinline__ float x2_lane1(f32x2 v) {
+    float l0, l1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(v));
+    return l1;
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// fmaf on each lane (a * b + c)
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    return x2_pack(fmaf(x2_lane0(a), x2_lane0(b), x2_lane0(c)), fmaf(x2_lane1(a), x2_lane1(b), x2_lane1(c)));
+}
+// a * b - p on each lane: the error of the rounded product p = a * b
+__device__ __forceinline__ f32x2 x2_prod_err(f32x2 a, f32x2 b, f32x2 p) {
+    return x2_pack(fmaf(x2_lane0(a), x2_lane0(b), -x2_lane0(p)), fmaf(x2_lane1(a), x2_lane1(b), -x2_lane1(p)));
+}
+
+struct ffx2 {
+    f32x2 hi, lo;
+};
+__device__ __forceinline__ ffx2 ffx2_both(ff a) { return ffx2{x2_pack(a.hi, a.hi), x2_pack(a.lo, a.lo)}; }
+__device__ __forceinline__ ff ffx2_lane0(const ffx2& a) { return ff{x2_lane0(a.hi), x2_lane0(a.lo)}; }
+__device__ __forceinline__ ff ffx2_lane1(const ffx2& a) { return ff{x2_lane1(a.hi), x2_lane1(a.lo)}; }
+
+__device__ __forceinline__ ffx2 ffx2_two_sum(f32x2 a, f32x2 b) {             // two_sum
+    const f32x2 s = x2_add(a, b), bb = x2_sub(s, a);
+    return ffx2{s, x2_add(x2_sub(a, x2_sub(s, bb)), x2_sub(b, bb))};
+}
+__device__ __forceinline__ ffx2 ffx2_renorm(const ffx2& a) {                  // ff_renorm
+    const f32x2 s = x2_add(a.hi, a.lo);
+    return ffx2{s, x2_sub(a.lo, x2_sub(s, a.hi))};
+}
+__device__ __forceinline__ ffx2 ffx2_add_big_u(const ffx2& a, const ffx2& b) {   // ff_add_big_u
+    const f32x2 s = x2_add(a.hi, b.hi);
+    return ffx2{s, x2_add(x2_sub(b.hi, x2_sub(s, a.hi)), x2_add(a.lo, b.lo))};
+}
+// ff_add_big_u(a, ff_neg(b)), with the negation folded into subtractions
+__device__ __forceinline__ ffx2 ffx2_sub_big_u(const ffx2& a, const ffx2& b) {
+    const f32x2 s = x2_sub(a.hi, b.hi);
+    return ffx2{s, x2_add(x2_sub(x2_sub(a.hi, s), b.hi), x2_sub(a.lo, b.lo))};
+}
+__device__ __forceinline__ ffx2 ffx2_mul_u(const ffx2& a, const ffx2& b) {       // ff_mul_u
+    const f32x2 p = x2_mul(a.hi, b.hi);
+    f32x2 e = x2_prod_err(a.hi, b.hi, p);
+    e = x2_fma(a.hi, b.lo, e);
+    e = x2_fma(a.lo, b.hi, e);
+    return ffx2{p, e};
+}
+__device__ __forceinline__ ffx2 ffx2_mul_f_u(const ffx2& a, f32x2 b) {           // ff_mul_f_u
+    const f32x2 p = x2_mul(a.hi, b);
+    return ffx2{p, x2_fma(a.lo, b, x2_prod_err(a.hi, b, p))};
+}
+__device__ __forceinline__ ffx2 ffx2_add_big_u_x4(const ffx2& a, const ffx2& b) {   // ff_add_big_u_x4
+    const f32x2 four = x2_pack(4.0f, 4.0f);
+    const f32x2 s = x2_fma(four, b.hi, a.hi);
+    return ffx2{s, x2_add(x2_fma(four, b.hi, x2_sub(a.hi, s)), x2_fma(four, b.lo, a.lo))};
+}
+
 }  // namespace lbm

@@ -11,7 +11,8 @@
 //      the FP32 pipes);
 //   4. 24 P(s), P(s) = K0 + K1 s + K2 s^2 + s^3/6 + s^4/24 (step_f64.cuh), is evaluated in
 //      float-float with the factor 24 folded into the coefficients (so the s^3 and s^4 terms
-//      need no constant), opposite velocities sharing the even part; w f^eq_l = (w w_l / 24)
+//      need no constant), opposite velocities sharing the even part, two velocity pairs at a
+//      time in the lanes of packed FP32 (f32x2) registers; w f^eq_l = (w w_l / 24)
 //      rho * 24 P(s), the constant held in three FP32 terms so that no representation error
 //      of it biases every step, is assembled into a binary64 pattern with integer instructions;
 //   5. a second read of the populations (served by L1/L2, so DRAM sees each byte once)
@@ -198,24 +199,33 @@ __device__ __forceinline__ void collide_ff(const MomentsFix& m, const SRC& src, 
         const ff W0 = ff_mul_c3(rho, p.wsh[0]);
         dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_bits(ff_renorm(ff_mul_u(W0, k00)))));
     }
-    // Loop over the shells; each shell (2 or 4 pairs) is processed two pairs at a time, so
-    // two independent dependency chains are in flight per thread.
-    auto pair_out = [&](const PairInfo& pi, const ff& K0, const ff& K1, const ff& K2, const ff& W,
-                        double va, double vb) {
+    // Loop over the shells; each shell (2 or 4 pairs) is processed two pairs at a time, the
+    // float-float arithmetic of the two pairs in the two lanes of packed FP32 registers
+    // (ffx2: one f32x2 add, sub or mul for both; the same operations per lane as the scalar
+    // forms, so the results are those of ff.cuh's scalar functions).
+    const ffx2 A = ffx2_both(a), B = ffx2_both(b);
+    auto pairs_out = [&](const PairInfo& p0, const PairInfo& p1, const ffx2& K0, const ffx2& K1, const ffx2& K2,
+                         const ffx2& W) {
+        double v0a, v0b, v1a, v1b;
+        src.pair(p0, v0a, v0b);
+        src.pair(p1, v1a, v1b);
         // s = xi_A . u_s = c_x a + c_z b (left unnormalised)
-        const ff sx = ff_mul_f_u(a, pi.fcx), sz = ff_mul_f_u(b, pi.fcz);
-        const ff st = two_sum(sx.hi, sz.hi);
-        const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
-        const ff q = ff_mul_u(s, s);
+        const ffx2 sx = ffx2_mul_f_u(A, x2_pack(p0.fcx, p1.fcx)), sz = ffx2_mul_f_u(B, x2_pack(p0.fcz, p1.fcz));
+        const ffx2 st = ffx2_two_sum(sx.hi, sz.hi);
+        const ffx2 s{st.hi, x2_add(st.lo, x2_add(sx.lo, sz.lo))};
+        const ffx2 q = ffx2_mul_u(s, s);
         // 24 P = [24 K0 + q (24 K2 + q)] + s [24 K1 + 4 q]; |24 K0| ~ 24 > q |24 K2 + q|,
         // |24 K2| ~ 12 > q, |24 K1| ~ 24 > 4 q and the even part exceeds the odd one for |u| < 0.3
-        const ff Ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, q)));
-        const ff Od = ff_mul_u(s, ff_add_big_u_x4(K1, q));
-        const ff Pa = ff_mul_u(W, Ev), Pb = ff_mul_u(W, Od);
-        // w f^eq of the pair in binary64, then f' = (1 - w) g + w f^eq by one FP64 FMA each
-        const double Xp = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, Pb)));
-        const double Xm = ff_to_double_bits(ff_renorm(ff_add_big_u(Pa, ff_neg(Pb))));
-        dst.pair(pi, fma(p.one_m_omega_d, va, Xp), fma(p.one_m_omega_d, vb, Xm));
+        const ffx2 Ev = ffx2_add_big_u(K0, ffx2_mul_u(q, ffx2_add_big_u(K2, q)));
+        const ffx2 Od = ffx2_mul_u(s, ffx2_add_big_u_x4(K1, q));
+        const ffx2 Pa = ffx2_mul_u(W, Ev), Pb = ffx2_mul_u(W, Od);
+        // w f^eq of both populations of each pair in binary64, then f' = (1 - w) g + w f^eq
+        // by one FP64 FMA each
+        const ffx2 Xp = ffx2_renorm(ffx2_add_big_u(Pa, Pb)), Xm = ffx2_renorm(ffx2_sub_big_u(Pa, Pb));
+        dst.pair(p0, fma(p.one_m_omega_d, v0a, ff_to_double_bits(ffx2_lane0(Xp))),
+                 fma(p.one_m_omega_d, v0b, ff_to_double_bits(ffx2_lane0(Xm))));
+        dst.pair(p1, fma(p.one_m_omega_d, v1a, ff_to_double_bits(ffx2_lane1(Xp))),
+                 fma(p.one_m_omega_d, v1b, ff_to_double_bits(ffx2_lane1(Xm))));
     };
 #pragma unroll 1
     for (int sh = 1; sh < NSHELL; sh++) {
@@ -225,15 +235,10 @@ __device__ __forceinline__ void collide_ff(const MomentsFix& m, const SRC& src, 
         const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
         const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
         const ff W = ff_mul_c3(rho, p.wsh[sh]);
+        const ffx2 K0b = ffx2_both(K0), K1b = ffx2_both(K1), K2b = ffx2_both(K2), Wb = ffx2_both(W);
 #pragma unroll 1
-        for (int k = k0; k < k1; k += 2) {            // every shell has an even number of pairs
-            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
-            double v0a, v0b, v1a, v1b;
-            src.pair(p0, v0a, v0b);
-            src.pair(p1, v1a, v1b);
-            pair_out(p0, K0, K1, K2, W, v0a, v0b);
-            pair_out(p1, K0, K1, K2, W, v1a, v1b);
-        }
+        for (int k = k0; k < k1; k += 2)              // every shell has an even number of pairs
+            pairs_out(d_pairs[k], d_pairs[k + 1], K0b, K1b, K2b, Wb);
     }
 }
 
@@ -312,8 +317,9 @@ __device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, dou
     else site_ff(src, DstPush<false>{fout, ad, pbase}, p);
 }
 
-// 7 resident blocks per SM (72 registers, 28 warps): measured best; 8 spills
-__global__ void __launch_bounds__(BLOCK_Z, 7)
+// 8 resident blocks per SM (64 registers, 32 warps; a 4-byte spill): measured best with the
+// packed pair loop (7 blocks at 72 registers is 1.5-3% slower)
+__global__ void __launch_bounds__(BLOCK_Z, 8)
 k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
     tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
