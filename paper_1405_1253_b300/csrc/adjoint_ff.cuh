@@ -298,25 +298,31 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
 __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const int64_t* __restrict__ mom,
                                                 const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                 const AdjParamsFF& p, Tiling t, int b, int* sbase) {
-    const bool wall_tile = tile_is_wall(t, b);
-    if (!wall_tile) {
-        fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
-        __syncthreads();
-    }
+    // wall and interior tiles on separate paths (the tile kind is block-uniform), as tile_ff
     SiteAddr ad;
     bool wall;
+    if (tile_is_wall(t, b)) {
+        if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+        const LamOwn lsrc{lam_next, ad.dst(), p.plane};
+        const DstSource<true> dst{lam_out, ad, sbase};
+        if (mom) {
+            adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
+        } else {
+            const SrcGlobal<true, LoadNC> src{ft, ad, sbase};
+            adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC>>{src}, lsrc, dst, p);
+        }
+        return;
+    }
+    fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+    __syncthreads();
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
     const LamOwn lsrc{lam_next, ad.dst(), p.plane};
+    const DstSource<false> dst{lam_out, ad, sbase};
     if (mom) {
-        const MomStored ms{mom, p.plane, ad.dst()};
-        if (wall) adjoint_site_ff(ms, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
-        else adjoint_site_ff(ms, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
-    } else if (wall) {
-        const SrcGlobal<true, LoadNC> src{ft, ad, sbase};
-        adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC>>{src}, lsrc, DstSource<true>{lam_out, ad, sbase}, p);
+        adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
     } else {
         const SrcGlobal<false, LoadNC> src{ft, ad, sbase};
-        adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, DstSource<false>{lam_out, ad, sbase}, p);
+        adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, dst, p);
     }
 }
 
