@@ -17,6 +17,8 @@
 // increasing order, while every item depends only on items of the previous step (smaller
 // numbers), so the smallest blocked item always has all of its dependencies running.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "step_f32.cuh"
 #include "step_ff.cuh"
@@ -72,13 +74,18 @@ __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, 
     tile_f32<LD>(fin, fout, q, L.t, local);
 }
 
-// Resident blocks per SM requested from the compiler for a tile height of TZ threads
-// (keeps the float-float tile near 96 registers).
+// Resident blocks per SM requested from the compiler for a tile height of TZ threads.  The
+// per-step kernel takes the register budgets of the single-lattice kernels: 32 warps per SM
+// for the float-float tile (64 registers, as k_step_ff) and 24 for the FP32 tile (80, as
+// k_step_f32).  The persistent kernel, which carries its queue and barrier state through
+// every tile, keeps 20 warps (96 registers; at 64 it spills 168 bytes).
+template <class P, int TZ>
+constexpr int ens_step_min_blocks() { return (std::is_same<P, StepParamsFF>::value ? 1024 : 768) / TZ; }
 template <int TZ>
-constexpr int ens_min_blocks() { return TZ == 64 ? 10 : TZ == 128 ? 5 : 2; }
+constexpr int ens_persistent_min_blocks() { return TZ == 64 ? 10 : TZ == 128 ? 5 : 2; }
 
 template <class P, int TZ>
-__global__ void __launch_bounds__(TZ, ens_min_blocks<TZ>())
+__global__ void __launch_bounds__(TZ, ens_step_min_blocks<P, TZ>())
 k_ens_step(const EnsLattice* __restrict__ lats, int n, P q, int s) {
     __shared__ int sbase[Q];
     const int b = blockIdx.x;
@@ -113,7 +120,7 @@ __device__ __forceinline__ bool ens_wait(const unsigned int* ctr, unsigned int n
 constexpr int ENS_CACHE = 64;
 
 template <class P, int TZ>
-__global__ void __launch_bounds__(TZ, ens_min_blocks<TZ>())
+__global__ void __launch_bounds__(TZ, ens_persistent_min_blocks<TZ>())
 k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_tiles,
                  EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
     __shared__ int sbase[Q];

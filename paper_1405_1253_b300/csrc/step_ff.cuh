@@ -307,17 +307,17 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
 template <class LD>
 __device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, double* __restrict__ fout,
                                             const StepParamsFF& p, Tiling t, int b, int* pbase) {
-    const bool wall_tile = tile_is_wall(t, b);
-    if (!wall_tile) {
-        fill_push_bases(pbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
-        __syncthreads();
-    }
     SiteAddr ad;
     bool wall;
+    if (tile_is_wall(t, b)) {                       // separate block-uniform paths, as tile_ff
+        if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+        site_ff(SrcOwn<LD>{fin, ad.dst(), p.plane}, DstPush<true>{fout, ad, pbase}, p);
+        return;
+    }
+    fill_push_bases(pbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+    __syncthreads();
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    const SrcOwn<LD> src{fin, ad.dst(), p.plane};
-    if (wall) site_ff(src, DstPush<true>{fout, ad, pbase}, p);
-    else site_ff(src, DstPush<false>{fout, ad, pbase}, p);
+    site_ff(SrcOwn<LD>{fin, ad.dst(), p.plane}, DstPush<false>{fout, ad, pbase}, p);
 }
 
 // 8 resident blocks per SM (64 registers, 32 warps; a 4-byte spill): measured best with the
