@@ -23,6 +23,9 @@
 // 64-bit fixed-point sums of step_ff.cuh; the result A' + B'.xi + C'|xi|^2 (scaled back by
 // the block exponent) enters the binary64 output through FP64 adds and one FP64 FMA per
 // population.  FP64 instructions per site: 37 FMAs, 36 adds, the five moment conversions.
+// The float-float work of the two velocity pairs of each loop iteration runs in the two lanes
+// of packed FP32 registers (ffx2, ff.cuh), with each lane's terms added to the sums in pair
+// order: the results are those of the scalar form, bit for bit.
 #pragma once
 #include "step_ff.cuh"
 
@@ -58,6 +61,36 @@ __device__ __forceinline__ ff ff_add_big_u_x2(ff a, ff b) {
 
 // Renormalisation without an ordering assumption (the sum may have cancelled).
 __device__ __forceinline__ ff ff_renorm2(ff a) { return two_sum(a.hi, a.lo); }
+
+// Packed two-lane forms of the adjoint's float-float operations (lane-wise the operations of
+// the scalar functions, so the results are the same bits).
+__device__ __forceinline__ ffx2 ffx2_add_u(const ffx2& a, const ffx2& b) {            // ff_add_u
+    const ffx2 s = ffx2_two_sum(a.hi, b.hi);
+    return ffx2{s.hi, x2_add(s.lo, x2_add(a.lo, b.lo))};
+}
+__device__ __forceinline__ ffx2 ffx2_sub_u(const ffx2& a, const ffx2& b) {            // ff_add_u(a, ff_neg(b))
+    const f32x2 s = x2_sub(a.hi, b.hi), bb = x2_sub(s, a.hi);
+    const f32x2 e = x2_sub(x2_sub(a.hi, x2_sub(s, bb)), x2_add(b.hi, bb));
+    return ffx2{s, x2_add(e, x2_sub(a.lo, b.lo))};
+}
+__device__ __forceinline__ ffx2 ffx2_mul_c3_u(const ffx2& a, const ff3& c) {          // ff_mul_c3_u
+    const f32x2 p = x2_mul(a.hi, x2_pack(c.hi, c.hi));
+    const float a0 = x2_lane0(a.hi), a1 = x2_lane1(a.hi);
+    float e0 = fmaf(a0, c.hi, -x2_lane0(p)), e1 = fmaf(a1, c.hi, -x2_lane1(p));
+    e0 = fmaf(a0, c.lo2, e0); e1 = fmaf(a1, c.lo2, e1);
+    e0 = fmaf(a0, c.lo, e0);  e1 = fmaf(a1, c.lo, e1);
+    e0 = fmaf(x2_lane0(a.lo), c.hi, e0); e1 = fmaf(x2_lane1(a.lo), c.hi, e1);
+    return ffx2{p, x2_pack(e0, e1)};
+}
+__device__ __forceinline__ ffx2 ffx2_add_big_u_x2(const ffx2& a, const ffx2& b) {     // ff_add_big_u_x2
+    const f32x2 two = x2_pack(2.0f, 2.0f);
+    const f32x2 s = x2_fma(two, b.hi, a.hi);
+    return ffx2{s, x2_add(x2_fma(two, b.hi, x2_sub(a.hi, s)), x2_fma(two, b.lo, a.lo))};
+}
+__device__ __forceinline__ ffx2 ffx2_scale(const ffx2& a, float k) {                  // exact products (k = 2^n)
+    const f32x2 kk = x2_pack(k, k);
+    return ffx2{x2_mul(a.hi, kk), x2_mul(a.lo, kk)};
+}
 
 // binary64 bit pattern of x -> float-float of x * 2^-(S >> 20), S = (E_block - 1023) << 20 a
 // signed shift of the exponent field.  The value after scaling must stay below 2^127 in
@@ -207,28 +240,48 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         sm.Bx = ff_make(0.0f, 0.0f);
         sm.Bz = ff_make(0.0f, 0.0f);
     }
-    auto pair_sums = [&](const PairInfo& pi, const ff& K0, const ff& K1, const ff& K2, const ff& H,
-                         const ff3& W, const ff& c6, const ff& c4, double va, double vb) {
-        const ff la = bits_to_ff_scaled((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va), S);
-        const ff lb = bits_to_ff_scaled((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb), S);
-        const ff ls = ff_mul_c3_u(ff_add_u(la, lb), W);
-        const ff ld = ff_mul_c3_u(ff_add_u(la, ff_neg(lb)), W);
-        const ff sx = ff_mul_f_u(a, pi.fcx), sz = ff_mul_f_u(b, pi.fcz);
-        const ff st = two_sum(sx.hi, sz.hi);
-        const ff s = ff_make(st.hi, st.lo + (sx.lo + sz.lo));
-        const ff q = ff_mul_u(s, s);
-        const ff P1 = ff_mul_u(ld, s), P2 = ff_mul_u(ls, s);
-        const ff ev = ff_add_big_u(K0, ff_mul_u(q, ff_add_big_u(K2, q)));     // 24 K0 + q (24 K2 + q)
-        const ff od = ff_add_big_u_x4(K1, q);                                 // 24 K1 + 4 q
-        const ff e1 = ff_add_big_u(K1, ff_mul_f_u(q, 12.0f));                 // 24 K1 + 12 q
-        const ff t2 = ff_add_big_u_x2(K2, q);                                 // 24 K2 + 2 q
-        sm.A = ff_add_u(sm.A, ff_add_u(ff_mul_u(ls, ev), ff_mul_u(P1, od)));
-        const ff bt = ff_add_u(ff_mul_u(ld, e1), ff_mul_pow2(ff_mul_u(P2, t2), 2.0f));
-        sm.Bx = ff_add_u(sm.Bx, ff_mul_f_u(bt, pi.fcx));
-        sm.Bz = ff_add_u(sm.Bz, ff_mul_f_u(bt, pi.fcz));
-        sm.U = ff_add_u(sm.U, ff_add_u(ff_mul_u(ls, e1), ff_mul_f_u(P1, 24.0f)));
-        const ff hq = ff_add_big_u(H, ff_mul_u(c6, q));
-        sm.C = ff_add_u(sm.C, ff_add_u(ff_mul_u(ls, hq), ff_mul_u(c4, P1)));
+    // the two pairs of each iteration in the lanes of packed FP32 registers; each lane's terms
+    // are added to the scalar sums in pair order, as the scalar loop does
+    const ffx2 A2 = ffx2_both(a), B2 = ffx2_both(b);
+    auto pair2_sums = [&](const PairInfo& p0, const PairInfo& p1, const ffx2& K0, const ffx2& K1, const ffx2& K2,
+                          const ffx2& H, const ff3& W, const ffx2& c6, const ffx2& c4) {
+        double v0a, v0b, v1a, v1b;
+        lsrc.pair(p0, v0a, v0b);
+        lsrc.pair(p1, v1a, v1b);
+        const ff la0 = bits_to_ff_scaled((uint32_t)__double2hiint(v0a), (uint32_t)__double2loint(v0a), S);
+        const ff lb0 = bits_to_ff_scaled((uint32_t)__double2hiint(v0b), (uint32_t)__double2loint(v0b), S);
+        const ff la1 = bits_to_ff_scaled((uint32_t)__double2hiint(v1a), (uint32_t)__double2loint(v1a), S);
+        const ff lb1 = bits_to_ff_scaled((uint32_t)__double2hiint(v1b), (uint32_t)__double2loint(v1b), S);
+        const ffx2 la{x2_pack(la0.hi, la1.hi), x2_pack(la0.lo, la1.lo)};
+        const ffx2 lb{x2_pack(lb0.hi, lb1.hi), x2_pack(lb0.lo, lb1.lo)};
+        const ffx2 ls = ffx2_mul_c3_u(ffx2_add_u(la, lb), W);
+        const ffx2 ld = ffx2_mul_c3_u(ffx2_sub_u(la, lb), W);
+        const f32x2 fcx = x2_pack(p0.fcx, p1.fcx), fcz = x2_pack(p0.fcz, p1.fcz);
+        const ffx2 sx = ffx2_mul_f_u(A2, fcx), sz = ffx2_mul_f_u(B2, fcz);
+        const ffx2 st = ffx2_two_sum(sx.hi, sz.hi);
+        const ffx2 s{st.hi, x2_add(st.lo, x2_add(sx.lo, sz.lo))};
+        const ffx2 q = ffx2_mul_u(s, s);
+        const ffx2 P1 = ffx2_mul_u(ld, s), P2 = ffx2_mul_u(ls, s);
+        const ffx2 ev = ffx2_add_big_u(K0, ffx2_mul_u(q, ffx2_add_big_u(K2, q)));
+        const ffx2 od = ffx2_add_big_u_x4(K1, q);
+        const ffx2 e1 = ffx2_add_big_u(K1, ffx2_mul_f_u(q, x2_pack(12.0f, 12.0f)));
+        const ffx2 t2 = ffx2_add_big_u_x2(K2, q);
+        const ffx2 tA = ffx2_add_u(ffx2_mul_u(ls, ev), ffx2_mul_u(P1, od));
+        const ffx2 bt = ffx2_add_u(ffx2_mul_u(ld, e1), ffx2_scale(ffx2_mul_u(P2, t2), 2.0f));
+        const ffx2 tx = ffx2_mul_f_u(bt, fcx), tz = ffx2_mul_f_u(bt, fcz);
+        const ffx2 tU = ffx2_add_u(ffx2_mul_u(ls, e1), ffx2_mul_f_u(P1, x2_pack(24.0f, 24.0f)));
+        const ffx2 hq = ffx2_add_big_u(H, ffx2_mul_u(c6, q));
+        const ffx2 tC = ffx2_add_u(ffx2_mul_u(ls, hq), ffx2_mul_u(c4, P1));
+        sm.A = ff_add_u(sm.A, ffx2_lane0(tA));
+        sm.Bx = ff_add_u(sm.Bx, ffx2_lane0(tx));
+        sm.Bz = ff_add_u(sm.Bz, ffx2_lane0(tz));
+        sm.U = ff_add_u(sm.U, ffx2_lane0(tU));
+        sm.C = ff_add_u(sm.C, ffx2_lane0(tC));
+        sm.A = ff_add_u(sm.A, ffx2_lane1(tA));
+        sm.Bx = ff_add_u(sm.Bx, ffx2_lane1(tx));
+        sm.Bz = ff_add_u(sm.Bz, ffx2_lane1(tz));
+        sm.U = ff_add_u(sm.U, ffx2_lane1(tU));
+        sm.C = ff_add_u(sm.C, ffx2_lane1(tC));
     };
 #pragma unroll 1
     for (int sh = 1; sh < NSHELL; sh++) {
@@ -238,17 +291,11 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
         const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
         const ff H = ff_add_u(h00, ff_mul_f_u(ff_add_u(h01, ff_mul_f_u(h02, C2)), C2));
-        const ff3 W = p.wsh[sh];
-        const ff c6 = p.c6[sh], c4 = p.c4[sh];
+        const ffx2 K0b = ffx2_both(K0), K1b = ffx2_both(K1), K2b = ffx2_both(K2), Hb = ffx2_both(H);
+        const ffx2 c6 = ffx2_both(p.c6[sh]), c4 = ffx2_both(p.c4[sh]);
 #pragma unroll 1
-        for (int k = k0; k < k1; k += 2) {
-            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
-            double v0a, v0b, v1a, v1b;
-            lsrc.pair(p0, v0a, v0b);
-            lsrc.pair(p1, v1a, v1b);
-            pair_sums(p0, K0, K1, K2, H, W, c6, c4, v0a, v0b);
-            pair_sums(p1, K0, K1, K2, H, W, c6, c4, v1a, v1b);
-        }
+        for (int k = k0; k < k1; k += 2)
+            pair2_sums(d_pairs[k], d_pairs[k + 1], K0b, K1b, K2b, Hb, p.wsh[sh], c6, c4);
     }
     // -- A', B', C' (times omega, in units of the block exponent) ---------------------------
     const ff A = ff_mul_c3(ff_renorm2(sm.A), p.inv24);
@@ -268,6 +315,7 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         const double v0 = lsrc.template again<0>();
         dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_scaled(Ap, S)));
     }
+    const ffx2 PHX = ffx2_both(phx), PHZ = ffx2_both(phz);
     // even part A' + C'|xi|^2 once per shell, odd part B'.xi once per pair, each rounded to
     // binary64; the sum and the relaxation are FP64 (the FP64 pipe has room for the adds,
     // the issue slots of a float-float add and a second assembly per population it saves)
@@ -281,14 +329,13 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
             double v0a, v0b, v1a, v1b;
             lsrc.pair(p0, v0a, v0b);
             lsrc.pair(p1, v1a, v1b);
-            auto out = [&](const PairInfo& pi, double va, double vb) {
-                const ff ox = ff_mul_f_u(phx, pi.fcx), oz = ff_mul_f_u(phz, pi.fcz);
-                const ff ot = two_sum(ox.hi, oz.hi);
-                const double od = ff_to_double_scaled(ff_renorm2(ff_make(ot.hi, ot.lo + (ox.lo + oz.lo))), S);
-                dst.pair(pi, fma(p.one_m_omega_d, va, ev + od), fma(p.one_m_omega_d, vb, ev - od));
-            };
-            out(p0, v0a, v0b);
-            out(p1, v1a, v1b);
+            // B'.xi of both pairs in the two lanes
+            const ffx2 ox = ffx2_mul_f_u(PHX, x2_pack(p0.fcx, p1.fcx)), oz = ffx2_mul_f_u(PHZ, x2_pack(p0.fcz, p1.fcz));
+            const ffx2 ot = ffx2_two_sum(ox.hi, oz.hi);
+            const ffx2 o = ffx2_two_sum(ot.hi, x2_add(ot.lo, x2_add(ox.lo, oz.lo)));     // ff_renorm2
+            const double od0 = ff_to_double_scaled(ffx2_lane0(o), S), od1 = ff_to_double_scaled(ffx2_lane1(o), S);
+            dst.pair(p0, fma(p.one_m_omega_d, v0a, ev + od0), fma(p.one_m_omega_d, v0b, ev - od0));
+            dst.pair(p1, fma(p.one_m_omega_d, v1a, ev + od1), fma(p.one_m_omega_d, v1b, ev - od1));
         }
     }
 }
