@@ -328,8 +328,9 @@ k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsF
     tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
 }
 
-// One step that also records every site's moments (for the adjoint of this step).
-__global__ void __launch_bounds__(BLOCK_Z, 7)
+// One step that also records every site's moments (for the adjoint of this step); 8 blocks
+// per SM as k_step_ff.
+__global__ void __launch_bounds__(BLOCK_Z, 8)
 k_step_ff_moments(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t,
                   int64_t* __restrict__ mom) {
     __shared__ int sbase[Q];
@@ -362,7 +363,7 @@ inline StepParamsFF ff_params(const StepParams& p, const double* w_shell) {
     return q;
 }
 
-__global__ void __launch_bounds__(BLOCK_Z, 7)
+__global__ void __launch_bounds__(BLOCK_Z, 8)      // 8 blocks per SM: 2% faster than 7
 k_step_ff_push(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int pbase[Q];
     tile_ff_push<LoadNC>(fin, fout, p, t, blockIdx.x, pbase);

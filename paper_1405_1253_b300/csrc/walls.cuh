@@ -112,7 +112,8 @@ __device__ __forceinline__ void thermal_gather(const ThermalSrc<T, LoadNC>& src,
     static_for<Q>([&](auto l) { g[l.value] = src.template first<decltype(l)::value>(); });
 }
 
-// One step with thermal walls (tiling t = make_tiling: wall tiles first).
+// One step with thermal walls (tiling t = make_tiling: wall tiles first).  7 blocks per SM:
+// at 8 the wall code spills 84 bytes and the step is no faster.
 __global__ void __launch_bounds__(BLOCK_Z, 7)
 k_step_ff_thermal(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t,
                   ThermalWall w) {
