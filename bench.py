@@ -57,11 +57,20 @@ KERNEL_SOURCES = {
 }
 
 
+def code_of(text: str) -> str:
+    """C++ source without comments and with whitespace runs collapsed (string literals in the
+    kernel headers hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash(kernel: str) -> str:
+    """Hash of the code (not the comments) of the sources that define a kernel."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1405_1253_b300", "csrc")
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(code_of(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -374,8 +374,9 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
 }
 
 // Two register budgets: 5 resident blocks per SM (96 registers, 20 warps; 4.6% faster than 4
-// blocks with 114 registers on large lattices) and 7 (72 registers, a small spill; 4% more time
-// per block, but one wave where the 5-block form needs two, as on 256 x 512).
+// blocks with 114 registers on large lattices) and 7 (72 registers; with the packed pair loops
+// it spills 128-260 bytes and takes about the same total time on large lattices, but it needs
+// one wave where the 5-block form needs two, as on 256 x 512).
 template <int MINB>
 __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
