@@ -370,6 +370,14 @@ int lbm_test_oob_count(unsigned int *out);
  * The paper has no counterpart.                                                       */
 int lbm_test_fail_alloc(int n);
 
+/* Test hook for the packed float-float arithmetic of the step and adjoint kernels (two values
+ * in the lanes of B300's packed FP32 registers): runs n seeded pairs of operands through every
+ * packed operation and its scalar form on the current device and stores in *mismatches the
+ * number of result words whose bits differ (0 when each lane reproduces the scalar form).
+ * Synchronises the device.  LBM_EINVAL for n < 1 or a NULL pointer.  The paper has no
+ * counterpart.                                                                          */
+int lbm_test_packed_ff(int n, unsigned long long seed, unsigned long long *mismatches);
+
 /* Message of the last failed call on this thread ("" if none).                        */
 const char *lbm_last_error(void);
 

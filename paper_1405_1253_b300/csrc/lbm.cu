@@ -25,6 +25,7 @@
 #include "walls.cuh"
 #include "adjoint_walls.cuh"
 #include "ensemble.cuh"
+#include "selftest.cuh"
 
 using namespace lbm;
 
@@ -307,6 +308,21 @@ int lbm_test_oob_count(unsigned int* out) {
 
 int lbm_test_fail_alloc(int n) {
     g_fail_alloc.store(n < 0 ? -1 : n);
+    return LBM_OK;
+}
+
+int lbm_test_packed_ff(int n, unsigned long long seed, unsigned long long* mismatches) {
+    if (n < 1 || !mismatches) return fail(LBM_EINVAL, "n = %d, mismatches %p", n, (void*)mismatches);
+    unsigned long long* d = nullptr;
+    if (dev_malloc(&d, sizeof *d) != cudaSuccess) return fail(LBM_ENOMEM, "cannot allocate the mismatch count");
+    cudaError_t e = cudaMemset(d, 0, sizeof *d);
+    if (e == cudaSuccess) {
+        k_selftest_ffx2<<<std::min((n + 255) / 256, 4096), 256>>>(n, seed, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(mismatches, d, sizeof *d, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "packed float-float self-test: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 

@@ -81,6 +81,7 @@ _SIGS = {
     "lbm_slabs_step": (_i, [_vp, _i, _i]),
     "lbm_slabs_gather": (_i, [_vp]),
     "lbm_test_fail_alloc": (_i, [_i]),
+    "lbm_test_packed_ff": (_i, [_i, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "lbm_test_oob_count": (_i, [ctypes.POINTER(ctypes.c_uint)]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -94,6 +95,14 @@ def test_fail_alloc(n: int):
     """Refuse the n-th next device allocation of the library (n < 0: cancel); for tests of
     the error paths."""
     _lib.lbm_test_fail_alloc(int(n))
+
+
+def test_packed_ff(n: int, seed: int) -> int:
+    """Result words in which a packed float-float operation differs from its scalar form, over
+    n seeded operand pairs (lbm_test_packed_ff)."""
+    out = ctypes.c_ulonglong(0)
+    _check(_lib.lbm_test_packed_ff(int(n), ctypes.c_ulonglong(seed), ctypes.byref(out)))
+    return out.value
 
 
 def test_oob_count() -> int:
