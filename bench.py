@@ -241,6 +241,21 @@ def time_variant(torch, lbm, lat, prec, steps, warmup, stream):
     return ms
 
 
+def bench_large(torch, lbm, steps, stream):
+    """The precision configuration's lattice (4096 x 8192, 33.6 M sites, ~222 waves of blocks
+    per launch against ~14 on 1024 x 2048): step throughput of both storage precisions, to
+    show what the headline lattice loses to the ramp-up and drain of each launch."""
+    lat = W.PRECISION_4096x8192
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps"}
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6400.0))
+    for prec in ("f64_ff", "f32"):
+        ms = time_variant(torch, lbm, lat, prec, steps, 3, stream)
+        torch.cuda.empty_cache()
+        gbs = 2 * Q * BYTES_PER_POP[prec] * lat.sites / (ms * 1e-3) / 1e9
+        out[prec] = {"ms_per_step": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+    return out
+
+
 def bench_ensemble(torch, lbm, prec, steps, stream):
     """The 48-lattice ensemble (16 x 256x512, 16 x 512x1024, 16 x 384x1536): autotuned,
     captured once as a CUDA graph of `steps` steps, replayed and timed."""
@@ -535,6 +550,7 @@ def run_ours(args):
         extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
         extras["push_vs_pull"] = bench_push(torch, lbm, lat, 200, stream)
         extras["walls"] = bench_walls(torch, lbm, lat, 200, stream)
+        extras["large_lattice"] = bench_large(torch, lbm, 50, stream)
 
     if rank != 0:
         return
@@ -586,7 +602,8 @@ def main():
     ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, adjoint, slab, push and FP32-error sections")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble, adjoint, slab, push, wall, large-lattice and FP32-error sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
