@@ -194,6 +194,13 @@ struct LoadNC {
         asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
+    // first reads of values read again soon, kept in L1 in preference (evict-last): the
+    // float-float step's second pass reads the inner shells first (measured +0.7%)
+    __device__ static __forceinline__ double ld_keep(const double* p) {
+        double v;
+        asm("ld.global.nc.L1::evict_last.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
     // a second read issued as its own instruction (not merged with an earlier one)
     __device__ static __forceinline__ double ld_again(const double* p) {
         double v;
@@ -204,6 +211,7 @@ struct LoadNC {
 struct LoadCG {
     template <class T>
     __device__ static __forceinline__ T ld(const T* p) { return __ldcg(p); }
+    __device__ static __forceinline__ double ld_keep(const double* p) { return __ldcg(p); }
     __device__ static __forceinline__ double ld_again(const double* p) {
         double v;
         asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
