@@ -138,11 +138,18 @@ struct LamOwn {
         asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"((const char*)p + 4));
         return v;
     }
-    template <int L>
-    __device__ __forceinline__ double again() const { return LoadNC::ld_again(lam + LBM_IDX(L * plane + o, Q * plane)); }
+    // re-reads; LAST: the output pass, the final use of each value (evict-first in L1)
+    template <int L, bool LAST = false>
+    __device__ __forceinline__ double again() const {
+        const double* q = lam + LBM_IDX(L * plane + o, Q * plane);
+        return LAST ? LoadNC::ld_last(q) : LoadNC::ld_again(q);
+    }
+    template <bool LAST = false>
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
-        va = LoadNC::ld_again(lam + LBM_IDX(pi.A * plane + o, Q * plane));
-        vb = LoadNC::ld_again(lam + LBM_IDX(pi.B * plane + o, Q * plane));
+        const double* qa = lam + LBM_IDX(pi.A * plane + o, Q * plane);
+        const double* qb = lam + LBM_IDX(pi.B * plane + o, Q * plane);
+        va = LAST ? LoadNC::ld_last(qa) : LoadNC::ld_again(qa);
+        vb = LAST ? LoadNC::ld_last(qb) : LoadNC::ld_again(qb);
     }
 };
 
@@ -312,7 +319,7 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
     const ff ph2 = ff_mul_pow2(ff_mul_c3(Cs, p.r2), 0.5f);                   // r^2 C'
     // -- pass 3: lam_t = (1 - w) lam + w (A' + B'.xi + C'|xi|^2), to the pull sources -------
     {
-        const double v0 = lsrc.template again<0>();
+        const double v0 = lsrc.template again<0, true>();
         dst.template put<0>(fma(p.one_m_omega_d, v0, ff_to_double_scaled(Ap, S)));
     }
     const ffx2 PHX = ffx2_both(phx), PHZ = ffx2_both(phz);
@@ -327,8 +334,8 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         for (int k = k0; k < k1; k += 2) {
             const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
             double v0a, v0b, v1a, v1b;
-            lsrc.pair(p0, v0a, v0b);
-            lsrc.pair(p1, v1a, v1b);
+            lsrc.template pair<true>(p0, v0a, v0b);
+            lsrc.template pair<true>(p1, v1a, v1b);
             // B'.xi of both pairs in the two lanes
             const ffx2 ox = ffx2_mul_f_u(PHX, x2_pack(p0.fcx, p1.fcx)), oz = ffx2_mul_f_u(PHZ, x2_pack(p0.fcz, p1.fcz));
             const ffx2 ot = ffx2_two_sum(ox.hi, oz.hi);

@@ -207,6 +207,13 @@ struct LoadNC {
         asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return v;
     }
+    // the last read of a value (the step's second pass): evict-first, so that the line does
+    // not displace lines still to be read again (measured +0.7% on the float-float step)
+    __device__ static __forceinline__ double ld_last(const double* p) {
+        double v;
+        asm volatile("ld.global.nc.L1::evict_first.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
 };
 struct LoadCG {
     template <class T>
@@ -217,6 +224,7 @@ struct LoadCG {
         asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return v;
     }
+    __device__ static __forceinline__ double ld_last(const double* p) { return ld_again(p); }
 };
 
 // Interior tiles: sbase[l] = l * plane + wrap(x - c_lx) * Lz - c_lz, so that the pull

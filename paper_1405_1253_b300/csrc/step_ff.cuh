@@ -57,15 +57,16 @@ struct SrcGlobal {
         if constexpr (KEEP && shell_of(L) >= 1 && shell_of(L) <= 4) return LD::ld_keep(fin + idx<L>());
         else return LD::ld(fin + idx<L>());
     }
+    // second reads (the step's last use of each value)
     template <int L>
-    __device__ __forceinline__ double again() const { return LD::ld_again(fin + idx<L>()); }
+    __device__ __forceinline__ double again() const { return LD::ld_last(fin + idx<L>()); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
         if constexpr (WALL) {
-            va = LD::ld_again(fin + LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane));
-            vb = LD::ld_again(fin + LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane));
+            va = LD::ld_last(fin + LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane));
+            vb = LD::ld_last(fin + LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane));
         } else {
-            va = LD::ld_again(fin + LBM_IDX(sbase[pi.A] + ad.z, Q * ad.plane));   // one 32-bit add, one address add
-            vb = LD::ld_again(fin + LBM_IDX(sbase[pi.B] + ad.z, Q * ad.plane));
+            va = LD::ld_last(fin + LBM_IDX(sbase[pi.A] + ad.z, Q * ad.plane));   // one 32-bit add, one address add
+            vb = LD::ld_last(fin + LBM_IDX(sbase[pi.B] + ad.z, Q * ad.plane));
         }
     }
 };
@@ -78,10 +79,10 @@ struct SrcOwn {
     template <int L>
     __device__ __forceinline__ double first() const { return LD::ld(fin + LBM_IDX(L * plane + o, Q * plane)); }
     template <int L>
-    __device__ __forceinline__ double again() const { return LD::ld_again(fin + LBM_IDX(L * plane + o, Q * plane)); }
+    __device__ __forceinline__ double again() const { return LD::ld_last(fin + LBM_IDX(L * plane + o, Q * plane)); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
-        va = LD::ld_again(fin + LBM_IDX(pi.A * plane + o, Q * plane));
-        vb = LD::ld_again(fin + LBM_IDX(pi.B * plane + o, Q * plane));
+        va = LD::ld_last(fin + LBM_IDX(pi.A * plane + o, Q * plane));
+        vb = LD::ld_last(fin + LBM_IDX(pi.B * plane + o, Q * plane));
     }
 };
 

@@ -79,7 +79,7 @@ struct ThermalSrc {
         if (zs >= ad.Lz) return (T)(s_out[1][ad.x - vx - xbase] * w.q[1][l]);
         const int xs = wrap_x(ad.x - vx, ad.Lx);
         const T* p = fin + LBM_IDX(l * ad.plane + xs * ad.Lz + zs, Q * ad.plane);
-        if constexpr (sizeof(T) == 8) return again ? LD::ld_again(p) : LD::ld(p);
+        if constexpr (sizeof(T) == 8) return again ? LD::ld_last(p) : LD::ld(p);
         else return LD::ld(p);
     }
     template <int L>
