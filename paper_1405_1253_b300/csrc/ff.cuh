@@ -199,14 +199,15 @@ __device__ __forceinline__ f32x2 x2_pack(float l0, float l1) {
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(l0), "f"(l1));
     return r;
 }
+// (the unpack writes both lanes; the other one goes to a scoped PTX register)
 __device__ __forceinline__ float x2_lane0(f32x2 v) {
-    float l0, l1;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(v));
+    float l0;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(l0) : "l"(v));
     return l0;
 }
 __device__ __forceinline__ float x2_lane1(f32x2 v) {
-    float l0, l1;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(l1) : "l"(v));
+    float l1;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(l1) : "l"(v));
     return l1;
 }
 __device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
