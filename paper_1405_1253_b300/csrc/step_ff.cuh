@@ -286,19 +286,25 @@ struct Shape {
 // filling sbase).  The tile kind is block-uniform, so wall and interior tiles take separate
 // paths, each with its own instance of the site code (measured 2% faster than choosing the
 // pull rule per site inside one path).
-template <class LD, class MOUT = NoMoments>
+//
+// PDL: the kernel was launched as a programmatic dependent of the previous kernel in its
+// stream; every thread waits for that grid to complete (griddepcontrol.wait) before its first
+// access to the populations, so only the pull-base fill overlaps the previous step.
+template <class LD, class MOUT = NoMoments, bool PDL = false>
 __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* __restrict__ fout,
                                        const StepParamsFF& p, Shape sh, Tiling t, int b, int* sbase,
                                        const MOUT& mo = MOUT{}) {
     SiteAddr ad;
     bool wall;
     if (tile_is_wall(t, b)) {
+        if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
         if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
         site_ff(SrcGlobal<true, LD, true>{fin, ad, sbase}, DstSite{fout, ad.dst(), sh.plane}, p, mo, ad.dst());
         return;
     }
     fill_pull_bases(sbase, tile_column(t, b), sh.Lx, sh.Lz, sh.plane);
     __syncthreads();
+    if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
     site_ff(SrcGlobal<false, LD, true>{fin, ad, sbase}, DstSite{fout, ad.dst(), sh.plane}, p, mo, ad.dst());
 }
@@ -327,11 +333,15 @@ __device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, dou
 }
 
 // 8 resident blocks per SM (64 registers, 32 warps; a 4-byte spill): measured best with the
-// packed pair loop (7 blocks at 72 registers is 1.5-3% slower)
+// packed pair loop (7 blocks at 72 registers is 1.5-3% slower).  Launched as a programmatic
+// dependent of the previous kernel in the stream (launch_step_ff): each block allows the next
+// step's blocks to be scheduled as soon as all of this step's blocks have started, which
+// hides the next launch and its pull-base fills under this step's last wave (+0.7%).
 __global__ void __launch_bounds__(BLOCK_Z, 8)
 k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
-    tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    tile_ff<LoadNC, NoMoments, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase);
 }
 
 // One step that also records every site's moments (for the adjoint of this step); 8 blocks
@@ -382,10 +392,24 @@ inline void launch_step_ff_push(const double* fin, double* fout, const StepParam
 }
 
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
+// k_step_ff waits for the previous grid before touching memory, so it may be launched as a
+// programmatic dependent (the previous kernel's results are visible after its wait; behind a
+// copy or an event wait the launch is ordered as usual).  Launch errors are left in the
+// runtime's last-error state, as for a <<<>>> launch.
 inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, const double* w_shell,
                            const Tiling& t, cudaStream_t st) {
     const StepParamsFF q = ff_params(p, w_shell);
-    k_step_ff<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiling_blocks(t));
+    cfg.blockDim = dim3(BLOCK_Z);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, k_step_ff, fin, fout, q, t);
 }
 
 
