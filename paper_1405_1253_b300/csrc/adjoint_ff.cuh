@@ -349,6 +349,9 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
 
 // One tile b of the tiling t (the step's tiling: wall tiles, then interior columns); the
 // moments come from f_t (ft) or, if ft is null, from the record mom.
+// PDL: launched with launch_pdl (every thread waits for the previous grid before its first
+// global access, as tile_ff).
+template <bool PDL = false>
 __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const int64_t* __restrict__ mom,
                                                 const double* __restrict__ lam_next, double* __restrict__ lam_out,
                                                 const AdjParamsFF& p, Tiling t, int b, int* sbase) {
@@ -356,6 +359,7 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
     SiteAddr ad;
     bool wall;
     if (tile_is_wall(t, b)) {
+        if constexpr (PDL) pdl_wait();
         if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
         const LamOwn lsrc{lam_next, ad.dst(), p.plane};
         const DstSource<true> dst{lam_out, ad, sbase};
@@ -369,6 +373,7 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
     }
     fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
     __syncthreads();
+    if constexpr (PDL) pdl_wait();
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
     const LamOwn lsrc{lam_next, ad.dst(), p.plane};
     const DstSource<false> dst{lam_out, ad, sbase};
@@ -389,7 +394,8 @@ __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
              AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
-    adjoint_tile_ff(ft, nullptr, lam_next, lam_out, p, t, blockIdx.x, sbase);
+    pdl_allow_next();
+    adjoint_tile_ff<true>(ft, nullptr, lam_next, lam_out, p, t, blockIdx.x, sbase);
 }
 
 // The same adjoint with the moments of f_t read from the forward step's record.
@@ -398,7 +404,8 @@ __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff_moments(const int64_t* __restrict__ mom, const double* __restrict__ lam_next,
                      double* __restrict__ lam_out, AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
-    adjoint_tile_ff(nullptr, mom, lam_next, lam_out, p, t, blockIdx.x, sbase);
+    pdl_allow_next();
+    adjoint_tile_ff<true>(nullptr, mom, lam_next, lam_out, p, t, blockIdx.x, sbase);
 }
 
 // Relative time per block of the 7-block form (measured on 1024 x 2048: 0.647 vs 0.623 ms).
@@ -457,9 +464,9 @@ inline void launch_adjoint_ff(const double* ft, const double* lam_next, double* 
     const int blocks = tiling_blocks(t);
     static TwoForms forms;
     if (pick_7_blocks(forms, blocks, k_adjoint_ff<5>, k_adjoint_ff<7>))
-        k_adjoint_ff<7><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+        launch_pdl(k_adjoint_ff<7>, blocks, BLOCK_Z, st, ft, lam_next, lam_out, q, t);
     else
-        k_adjoint_ff<5><<<blocks, BLOCK_Z, 0, st>>>(ft, lam_next, lam_out, q, t);
+        launch_pdl(k_adjoint_ff<5>, blocks, BLOCK_Z, st, ft, lam_next, lam_out, q, t);
 }
 
 inline void launch_adjoint_ff_moments(const int64_t* mom, const double* lam_next, double* lam_out,
@@ -469,9 +476,9 @@ inline void launch_adjoint_ff_moments(const int64_t* mom, const double* lam_next
     const int blocks = tiling_blocks(t);
     static TwoForms forms;
     if (pick_7_blocks(forms, blocks, k_adjoint_ff_moments<5>, k_adjoint_ff_moments<7>))
-        k_adjoint_ff_moments<7><<<blocks, BLOCK_Z, 0, st>>>(mom, lam_next, lam_out, q, t);
+        launch_pdl(k_adjoint_ff_moments<7>, blocks, BLOCK_Z, st, mom, lam_next, lam_out, q, t);
     else
-        k_adjoint_ff_moments<5><<<blocks, BLOCK_Z, 0, st>>>(mom, lam_next, lam_out, q, t);
+        launch_pdl(k_adjoint_ff_moments<5>, blocks, BLOCK_Z, st, mom, lam_next, lam_out, q, t);
 }
 
 }  // namespace lbm

@@ -242,6 +242,30 @@ __device__ __forceinline__ void fill_push_bases(int* pbase, int x, int Lx, int L
         pbase[l] = l * plane + wrap_x(x + d_vel[l][0], Lx) * Lz + d_vel[l][1];
 }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start while the
+// previous kernel in its stream is still running (once all of that kernel's blocks have
+// called pdl_allow_next or exited); every thread of it must call pdl_wait, which returns when
+// the previous grid has completed and its writes are visible, before its first access to
+// global memory.  Behind a copy or an event wait the launch is ordered as usual.
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch errors are left in the runtime's last-error state, as for a <<<>>> launch.
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int blocks, int threads, cudaStream_t st, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Compile-time loop: calls f(Tag<L>{}) for L = 0..N-1.
 template <int L>
 struct Tag { static constexpr int value = L; };

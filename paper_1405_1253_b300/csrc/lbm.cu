@@ -924,7 +924,7 @@ int lbm_record_moments(lbm_ctx* c, const double* f0, int n, double* work_a, doub
     double* w[2] = {work_a, work_b};
     for (int j = 0; j < n; j++) {
         const double* fin = j == 0 ? f0 : w[(j - 1) & 1];
-        k_step_ff_moments<<<tiling_blocks(t), BLOCK_Z, 0, c->stream>>>(fin, w[j & 1], q, t, moments[j]);
+        launch_pdl(k_step_ff_moments, tiling_blocks(t), BLOCK_Z, c->stream, fin, w[j & 1], q, t, moments[j]);
         LAUNCH_CHECK();
     }
     return LBM_OK;

@@ -141,8 +141,8 @@ __device__ __forceinline__ void tile_f32(const float* __restrict__ fin, float* _
 // every thread waits for the previous grid to complete before it reads or writes populations.
 __global__ void __launch_bounds__(BLOCK_Z)
 k_step_f32(const float* __restrict__ fin, float* __restrict__ fout, StepParamsF p, Tiling t) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_allow_next();
+    pdl_wait();
     tile_f32<LoadNC>(fin, fout, p, t, blockIdx.x);
 }
 
@@ -163,17 +163,7 @@ inline StepParamsF f32_params(const StepParams& p) {
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
 inline void launch_step_f32(const float* fin, float* fout, const StepParams& p, const Tiling& t, cudaStream_t st) {
     const StepParamsF q = f32_params(p);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(tiling_blocks(t));
-    cfg.blockDim = dim3(BLOCK_Z);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    (void)cudaLaunchKernelEx(&cfg, k_step_f32, fin, fout, q, t);
+    launch_pdl(k_step_f32, tiling_blocks(t), BLOCK_Z, st, fin, fout, q, t);
 }
 inline void launch_step_f32_push(const float* fin, float* fout, const StepParams& p, const Tiling& t,
                                  cudaStream_t st) {

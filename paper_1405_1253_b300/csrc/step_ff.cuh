@@ -297,14 +297,14 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
     SiteAddr ad;
     bool wall;
     if (tile_is_wall(t, b)) {
-        if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+        if constexpr (PDL) pdl_wait();
         if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
         site_ff(SrcGlobal<true, LD, true>{fin, ad, sbase}, DstSite{fout, ad.dst(), sh.plane}, p, mo, ad.dst());
         return;
     }
     fill_pull_bases(sbase, tile_column(t, b), sh.Lx, sh.Lz, sh.plane);
     __syncthreads();
-    if constexpr (PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if constexpr (PDL) pdl_wait();
     if (!ad.setup(sh.Lx, sh.Lz, sh.plane, t, b, wall)) return;
     site_ff(SrcGlobal<false, LD, true>{fin, ad, sbase}, DstSite{fout, ad.dst(), sh.plane}, p, mo, ad.dst());
 }
@@ -340,17 +340,19 @@ __device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, dou
 __global__ void __launch_bounds__(BLOCK_Z, 8)
 k_step_ff(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_allow_next();
     tile_ff<LoadNC, NoMoments, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase);
 }
 
 // One step that also records every site's moments (for the adjoint of this step); 8 blocks
-// per SM as k_step_ff.
+// per SM and programmatic dependent launch as k_step_ff.
 __global__ void __launch_bounds__(BLOCK_Z, 8)
 k_step_ff_moments(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t,
                   int64_t* __restrict__ mom) {
     __shared__ int sbase[Q];
-    tile_ff<LoadNC>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase, MomentsOut{mom, p.plane});
+    pdl_allow_next();
+    tile_ff<LoadNC, MomentsOut, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase,
+                                      MomentsOut{mom, p.plane});
 }
 
 inline ff ff_host(double v) {
@@ -392,24 +394,11 @@ inline void launch_step_ff_push(const double* fin, double* fout, const StepParam
 }
 
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).
-// k_step_ff waits for the previous grid before touching memory, so it may be launched as a
-// programmatic dependent (the previous kernel's results are visible after its wait; behind a
-// copy or an event wait the launch is ordered as usual).  Launch errors are left in the
-// runtime's last-error state, as for a <<<>>> launch.
+// k_step_ff waits for the previous grid before touching memory (launch_pdl).
 inline void launch_step_ff(const double* fin, double* fout, const StepParams& p, const double* w_shell,
                            const Tiling& t, cudaStream_t st) {
     const StepParamsFF q = ff_params(p, w_shell);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(tiling_blocks(t));
-    cfg.blockDim = dim3(BLOCK_Z);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    (void)cudaLaunchKernelEx(&cfg, k_step_ff, fin, fout, q, t);
+    launch_pdl(k_step_ff, tiling_blocks(t), BLOCK_Z, st, fin, fout, q, t);
 }
 
 
