@@ -150,9 +150,13 @@ __device__ __forceinline__ void adjoint_native_site(const T* __restrict__ ft, co
     });
 }
 
+// Both native forms are launched with launch_pdl (common.cuh): no prologue to overlap, but the
+// next adjoint step is scheduled during this one's last wave.
 __global__ void __launch_bounds__(BLOCK_Z)
 k_adjoint_native_f64(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
                      StepParams p) {
+    pdl_allow_next();
+    pdl_wait();
     adjoint_native_site(ft, lam_next, lam_out, p);
 }
 
@@ -162,6 +166,8 @@ k_adjoint_native_f64(const double* __restrict__ ft, const double* __restrict__ l
 __global__ void __launch_bounds__(BLOCK_Z, 7)
 k_adjoint_native_f32(const float* __restrict__ ft, const float* __restrict__ lam_next, float* __restrict__ lam_out,
                      StepParams p) {
+    pdl_allow_next();
+    pdl_wait();
     adjoint_native_site(ft, lam_next, lam_out, p);
 }
 

@@ -857,10 +857,10 @@ static void launch_adjoint(const lbm_ctx* c, const void* f_t, const void* lam_ne
     } else if (c->prec == LBM_F64_FF) {
         launch_adjoint_ff(fd, ld, od, p, quad_w_shell(), g_quad.r, make_tiling(c->Lx, c->Lz, BLOCK_Z), c->stream);
     } else if (c->prec == LBM_F64) {
-        k_adjoint_native_f64<<<grid, BLOCK_Z, 0, c->stream>>>(fd, ld, od, p);
+        launch_pdl(k_adjoint_native_f64, grid, BLOCK_Z, c->stream, fd, ld, od, p);
     } else {
-        k_adjoint_native_f32<<<grid, BLOCK_Z, 0, c->stream>>>((const float*)f_t, (const float*)lam_next,
-                                                              (float*)lam_out, p);
+        launch_pdl(k_adjoint_native_f32, grid, BLOCK_Z, c->stream, (const float*)f_t, (const float*)lam_next,
+                   (float*)lam_out, p);
     }
 }
 
