@@ -267,8 +267,8 @@ static void ctx_step(const lbm_ctx* c, const void* fin, void* fout, const StepPa
             k_step_f64_thermal<<<blocks, BLOCK_Z, 0, st>>>((const double*)fin, (double*)fout, p, t, c->tw);
             break;
         case LBM_F64_FF:
-            k_step_ff_thermal<<<blocks, BLOCK_Z, 0, st>>>((const double*)fin, (double*)fout,
-                                                          ff_params(p, quad_w_shell()), t, c->tw);
+            launch_pdl(k_step_ff_thermal, blocks, BLOCK_Z, st, (const double*)fin, (double*)fout,
+                       ff_params(p, quad_w_shell()), t, c->tw);
             break;
         default:
             k_step_f32_thermal<<<blocks, BLOCK_Z, 0, st>>>((const float*)fin, (float*)fout, f32_params(p), t, c->tw);

@@ -316,18 +316,20 @@ __device__ __forceinline__ void tile_ff(const double* __restrict__ fin, double* 
 
 // Push form of one tile: aligned reads of the site's own populations, results written
 // where they move to; pbase: Q ints of shared memory (push bases of interior tiles).
-template <class LD>
+template <class LD, bool PDL = false>
 __device__ __forceinline__ void tile_ff_push(const double* __restrict__ fin, double* __restrict__ fout,
                                             const StepParamsFF& p, Tiling t, int b, int* pbase) {
     SiteAddr ad;
     bool wall;
     if (tile_is_wall(t, b)) {                       // separate block-uniform paths, as tile_ff
+        if constexpr (PDL) pdl_wait();
         if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
         site_ff(SrcOwn<LD>{fin, ad.dst(), p.plane}, DstPush<true>{fout, ad, pbase}, p);
         return;
     }
     fill_push_bases(pbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
     __syncthreads();
+    if constexpr (PDL) pdl_wait();
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
     site_ff(SrcOwn<LD>{fin, ad.dst(), p.plane}, DstPush<false>{fout, ad, pbase}, p);
 }
@@ -384,13 +386,14 @@ inline StepParamsFF ff_params(const StepParams& p, const double* w_shell) {
 __global__ void __launch_bounds__(BLOCK_Z, 8)      // 8 blocks per SM: 2% faster than 7
 k_step_ff_push(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t) {
     __shared__ int pbase[Q];
-    tile_ff_push<LoadNC>(fin, fout, p, t, blockIdx.x, pbase);
+    pdl_allow_next();                   // launched with launch_pdl, as k_step_ff
+    tile_ff_push<LoadNC, true>(fin, fout, p, t, blockIdx.x, pbase);
 }
 
 inline void launch_step_ff_push(const double* fin, double* fout, const StepParams& p, const double* w_shell,
                                 const Tiling& t, cudaStream_t st) {
     const StepParamsFF q = ff_params(p, w_shell);
-    k_step_ff_push<<<tiling_blocks(t), BLOCK_Z, 0, st>>>(fin, fout, q, t);
+    launch_pdl(k_step_ff_push, tiling_blocks(t), BLOCK_Z, st, fin, fout, q, t);
 }
 
 // One step over the columns of tiling t (the whole lattice when t = make_tiling(Lx, Lz, BLOCK_Z)).

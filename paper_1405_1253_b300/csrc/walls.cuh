@@ -119,10 +119,12 @@ k_step_ff_thermal(const double* __restrict__ fin, double* __restrict__ fout, Ste
                   ThermalWall w) {
     __shared__ int sbase[Q];
     __shared__ double s_out[2][WALL_COLS];
+    pdl_allow_next();                   // launched with launch_pdl, as k_step_ff
     if (!tile_is_wall(t, blockIdx.x)) {
-        tile_ff<LoadNC>(fin, fout, p, t, blockIdx.x, sbase);
+        tile_ff<LoadNC, NoMoments, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase);
         return;
     }
+    pdl_wait();
     int xbase;
     SiteAddr ad;
     if (!thermal_wall_site(fin, p.Lx, p.Lz, p.plane, t, blockIdx.x, s_out, xbase, ad)) return;
