@@ -15,8 +15,11 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   propagate, bc ................ pinned (np.roll interior, bijection, reversibility, rest state);
                                  the wall RULE is a reading: the paper names the rows only
   collide ...................... pinned (mass, momentum + rho g, temperature invariants)
-  init_layers .................. pinned (isothermal hydrostatic slopes, pressure continuity)
+  init_layers, init_columns .... pinned (isothermal hydrostatic slopes, pressure continuity;
+                                 the column form equals the listed columns of the full one)
   moments ...................... pinned (round trip through the pinned equilibrium)
+  row_mean_T ................... pinned (closed-form tanh profile of the initial state, its
+                                 column average with modes, equilibria of chosen fields)
   widths ....................... pinned (closed form on a tanh profile)
   adjoint_step, loss/init adjoint  pinned (finite differences, dot-product identity)
 """
@@ -68,6 +71,8 @@ def _load():
                 "oracle_collide": (None, [i, i, d, d, dp, dp]),
                 "oracle_step": (None, [i, i, d, d, i, dp, dp]),
                 "oracle_init_layers": (None, [i, i, d, d, d, d, d, d, d, d, i, dp, dp, dp, dp, dp]),
+                "oracle_init_columns": (None, [i, i, d, d, d, d, d, d, d, d, i, dp, dp, dp, dp,
+                                               i, ip, dp]),
                 "oracle_moments": (None, [i, i, d, dp, dp, dp, dp, dp, i]),
                 "oracle_row_mean_T": (None, [i, i, dp, dp]),
                 "oracle_widths": (i, [i, dp, d, d, d, dp, dp]),
@@ -196,6 +201,21 @@ def init_layers(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt,
     lib.oracle_init_layers(int(Lx), int(Lz), float(grav), float(Tu), float(Tm), float(Td),
                            float(zlo0), float(zhi0), float(rho_ref), float(wt), K,
                            _p(amp_lo), _p(ph_lo), _p(amp_hi), _p(ph_hi), _p(f))
+    return f
+
+
+def init_columns(Lx, Lz, cols, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt,
+                 amp_lo, ph_lo, amp_hi, ph_hi) -> np.ndarray:
+    """Columns `cols` of the Lx x Lz initial state, as a [37, len(cols), Lz] array."""
+    lib = _load()
+    amp_lo, ph_lo, amp_hi, ph_hi = map(_f64, (amp_lo, ph_lo, amp_hi, ph_hi))
+    K = len(amp_lo)
+    cols = np.ascontiguousarray(np.asarray(cols, dtype=np.int32) % int(Lx))
+    f = np.empty((Q, len(cols), Lz))
+    lib.oracle_init_columns(int(Lx), int(Lz), float(grav), float(Tu), float(Tm), float(Td),
+                            float(zlo0), float(zhi0), float(rho_ref), float(wt), K,
+                            _p(amp_lo), _p(ph_lo), _p(amp_hi), _p(ph_hi), len(cols),
+                            cols.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(f))
     return f
 
 

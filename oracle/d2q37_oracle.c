@@ -499,21 +499,42 @@ static void layer_state(double z, double zl, double zh, double grav, double Tu, 
     *T = Tu + (Tm - Tu) * 0.5 * (1.0 - tanh((z - zh) / wt)) + (Td - Tm) * 0.5 * (1.0 - tanh((z - zl) / wt));
 }
 
+/* Column x of the Lx-column initial state into column j of an ncol-column array. */
+static void init_column(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
+                        double zlo0, double zhi0, double rho_ref, double wt, int K,
+                        const double *amp_lo, const double *ph_lo,
+                        const double *amp_hi, const double *ph_hi, int x, int ncol, int j, double *f) {
+    double zl = interface_height(zlo0, K, amp_lo, ph_lo, x, Lx);
+    double zh = interface_height(zhi0, K, amp_hi, ph_hi, x, Lx);
+    for (int k = 0; k < Lz; k++) {
+        double p, T, feq[NPOP];
+        layer_state(k + 0.5, zl, zh, grav, Tu, Tm, Td, rho_ref, wt, &p, &T);
+        equilibrium_with_derivs(p / T, 0.0, -0.5 * grav, T, feq, NULL, NULL);
+        for (int l = 0; l < NPOP; l++) f[ix(ncol, Lz, l, j, k)] = feq[l];
+    }
+}
+
 void oracle_init_layers(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
                         double zlo0, double zhi0, double rho_ref, double wt, int K,
                         const double *amp_lo, const double *ph_lo,
                         const double *amp_hi, const double *ph_hi, double *f) {
     oracle_setup();
-    for (int x = 0; x < Lx; x++) {
-        double zl = interface_height(zlo0, K, amp_lo, ph_lo, x, Lx);
-        double zh = interface_height(zhi0, K, amp_hi, ph_hi, x, Lx);
-        for (int k = 0; k < Lz; k++) {
-            double p, T, feq[NPOP];
-            layer_state(k + 0.5, zl, zh, grav, Tu, Tm, Td, rho_ref, wt, &p, &T);
-            equilibrium_with_derivs(p / T, 0.0, -0.5 * grav, T, feq, NULL, NULL);
-            for (int l = 0; l < NPOP; l++) f[ix(Lx, Lz, l, x, k)] = feq[l];
-        }
-    }
+    for (int x = 0; x < Lx; x++)
+        init_column(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt, K, amp_lo, ph_lo, amp_hi, ph_hi,
+                    x, Lx, x, f);
+}
+
+/* The same state restricted to the listed columns cols[0..ncol-1] of the Lx-column lattice
+ * (f: 37 x ncol x Lz), so that single columns of a large lattice can be checked. */
+void oracle_init_columns(int Lx, int Lz, double grav, double Tu, double Tm, double Td,
+                         double zlo0, double zhi0, double rho_ref, double wt, int K,
+                         const double *amp_lo, const double *ph_lo,
+                         const double *amp_hi, const double *ph_hi,
+                         int ncol, const int *cols, double *f) {
+    oracle_setup();
+    for (int j = 0; j < ncol; j++)
+        init_column(Lx, Lz, grav, Tu, Tm, Td, zlo0, zhi0, rho_ref, wt, K, amp_lo, ph_lo, amp_hi, ph_hi,
+                    cols[j], ncol, j, f);
 }
 
 /* ---------------------------------------------------------------------------

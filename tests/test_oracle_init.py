@@ -74,3 +74,16 @@ def test_modes_displace_the_interfaces():
         j = np.where(prof < mid_hi)[0][0]
         zcross = zc[60 + j - 1] + (mid_hi - prof[j - 1]) / (prof[j] - prof[j - 1])
         assert abs(zcross - zh[xi]) < 0.1
+
+
+def test_column_form_equals_the_full_initial_state():
+    """init_columns (single columns of a large lattice) is the full init restricted to the
+    listed columns, including columns listed twice and out of order."""
+    Lx, Lz, g = 17, 40, 1e-4
+    a_lo, p_lo = np.array([2.0, -1.0, 0.5]), np.array([0.3, 1.1, 4.0])
+    a_hi, p_hi = np.array([-1.5, 0.8, 0.2]), np.array([2.0, 0.2, 5.5])
+    args = (g, TU, TM, TD, 13.0, 27.0, 1.0, 3.0, a_lo, p_lo, a_hi, p_hi)
+    full = oracle.init_layers(Lx, Lz, *args)
+    cols = [16, 0, 5, 5, 11]
+    part = oracle.init_columns(Lx, Lz, cols, *args)
+    np.testing.assert_array_equal(part, full[:, cols, :])
