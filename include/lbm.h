@@ -53,15 +53,17 @@ enum {
 
 /* Population storage and collide arithmetic.
  *   LBM_F64     IEEE binary64 storage, collide in native FP64 arithmetic.
+ *   LBM_F32     FP32 storage, FP32 collide arithmetic (compensated moment sums; the
+ *               collide update is repaired to conserve mass, momentum + rho g and
+ *               internal energy).
+ *   value 2     reserved for FP32 storage of the deviation from a per-row FP64
+ *               reference state; not built, rejected with LBM_EINVAL.
  *   LBM_F64_FF  IEEE binary64 storage; moments summed in 64-bit integers, the rest of
  *               the collide in float-float arithmetic (pairs of FP32 carrying a ~48-bit
  *               significand) on the FP32 and integer pipes, one FP64 FMA per population
  *               for the relaxation; same storage and bytes as LBM_F64, results equal to
- *               it to ~1e-14 per step.
- *   LBM_F32     FP32 storage, FP32 collide arithmetic (compensated moment sums; the
- *               collide update is repaired to conserve mass, momentum + rho g and
- *               internal energy).                                                     */
-typedef enum { LBM_F64 = 0, LBM_F64_FF = 1, LBM_F32 = 2 } lbm_prec;
+ *               it to ~1e-14 per step.                                                 */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F64_FF = 3 } lbm_prec;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque */
 

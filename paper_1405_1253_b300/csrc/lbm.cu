@@ -345,7 +345,8 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     if (Lx < 1 || Lz < 6) return fail(LBM_EINVAL, "lattice %d x %d: need Lx >= 1, Lz >= 6", Lx, Lz);
     if ((long long)Q * Lx * Lz >= (1LL << 31))
         return fail(LBM_EINVAL, "lattice %d x %d too large: 37*Lx*Lz must be < 2^31", Lx, Lz);
-    if (prec < LBM_F64 || prec > LBM_F32) return fail(LBM_EINVAL, "unknown precision %d", prec);
+    if (prec != LBM_F64 && prec != LBM_F32 && prec != LBM_F64_FF)
+        return fail(LBM_EINVAL, "unknown precision %d", prec);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_EINVAL, "tau = %g must be > 0.5", tau);
     if (!(g >= 0.0) || !std::isfinite(g)) return fail(LBM_EINVAL, "g = %g must be >= 0", g);
     if (!buf0 || !buf1 || buf0 == buf1) return fail(LBM_EINVAL, "need two distinct device buffers");
