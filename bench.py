@@ -34,6 +34,7 @@ from paper_1405_1253_b300 import workloads as W  # noqa: E402
 Q = 37
 METRIC = "MLUPS and % HBM roofline, FP64 vs FP32-storage (stated error), adjoint/forward"
 REF_BUDGET_S = 120.0        # oracle seconds of one reference-arm run (warmup + timed steps)
+SPEC_HBM_GBS = 7700.0       # nominal B300 HBM3e bandwidth (context beside the measured copy peak)
 BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4}
 ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32"}
 KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32"}
@@ -113,6 +114,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s: float = 3.0):
+        """Block until the sampler has produced its first line (nvidia-smi takes a few hundred
+        ms to start), so that the timed region that follows is covered from its start."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.02)
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -154,6 +162,22 @@ def aggregate_ranks(ms_total: float, steps: int, sites_per_rank: int, world_size
         ms_total = float(t.item())
     ms_step = ms_total / steps
     return ms_total, ms_step, world_size * sites_per_rank / (ms_step * 1e-3) / 1e6
+
+
+def repeats_for(est_region_ms: float, window_s: float, world_size: int, lo: int = 3, hi: int = 2000,
+                device="cuda") -> int:
+    """Number of repeats of a timed region of about est_region_ms for window_s seconds of
+    coverage (at least lo, at most hi); with several ranks the largest estimate wins, so that
+    every rank runs the same number."""
+    r = int(np.ceil(window_s * 1e3 / max(est_region_ms, 1e-3)))
+    r = max(lo, min(hi, r))
+    if world_size > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([r], dtype=torch.int64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r = int(t.item())
+    return r
 
 
 def dist_setup():
@@ -241,24 +265,54 @@ def time_variant(torch, lbm, lat, prec, steps, warmup, stream):
     return ms
 
 
-def bench_large(torch, lbm, steps, stream):
-    """The precision configuration's lattice (4096 x 8192, 33.6 M sites, ~222 waves of blocks
-    per launch against ~14 on 1024 x 2048): step throughput of both storage precisions, to
-    show what the headline lattice loses to the ramp-up and drain of each launch."""
+def bench_precision(torch, lbm, steps, stream):
+    """The precision configuration: 4096 x 8192 (33.6 M sites, 128 modes), `steps` steps of
+    the FP32-storage step and of the FP64-accurate (float-float) step from the same seeded
+    initial state; relative L2 errors of rho and T and relative errors of both fronts' widths
+    of the FP32 run against the FP64-accurate one, the mass drift, and the throughput of each
+    (CUDA events around the stepping only; ~222 waves of blocks per launch against ~14 on
+    1024 x 2048)."""
     lat = W.PRECISION_4096x8192
-    out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps"}
     peak = float(measured_peaks()[0].get("hbm_gbs", 6400.0))
+    out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps, tau={lat.tau}, g={lat.grav}, {lat.K} modes (seed {lat.seed})"}
+    fields = {}
     for prec in ("f64_ff", "f32"):
-        ms = time_variant(torch, lbm, lat, prec, steps, 3, stream)
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
+        L.init_from(lat)
+        m0 = L.global_sums()[0]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        rho, _, _, T = L.moments()
+        widths = L.widths(lat.T_u, lat.T_m, lat.T_d)
+        m1 = L.global_sums()[0]
+        L.close()
         torch.cuda.empty_cache()
         gbs = 2 * Q * BYTES_PER_POP[prec] * lat.sites / (ms * 1e-3) / 1e9
-        out[prec] = {"ms_per_step": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak}
+        out[prec] = {"ms_per_step": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak,
+                     "widths": [float(v) for v in widths], "mass_rel_drift": float(abs(m1 - m0) / m0)}
+        fields[prec] = (rho, T, widths)
+    (r64, T64, w64), (r32, T32, w32) = fields["f64_ff"], fields["f32"]
+    out["rho_rel_l2"] = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
+    out["T_rel_l2"] = float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64))
+    out["T_max_abs"] = float(np.abs(T32 - T64).max())
+    out["width_rel_err"] = [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]
+    out["speedup_f32"] = out["f64_ff"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    out["error_bound"] = 1e-5
+    out["fields_within_bound"] = bool(out["rho_rel_l2"] < 1e-5 and out["T_rel_l2"] < 1e-5)
     return out
 
 
-def bench_ensemble(torch, lbm, prec, steps, stream):
-    """The 48-lattice ensemble (16 x 256x512, 16 x 512x1024, 16 x 384x1536): autotuned,
-    captured once as a CUDA graph of `steps` steps, replayed and timed."""
+def bench_ensemble(torch, lbm, prec, steps, stream, tune_steps=20):
+    """The 48-lattice ensemble (16 x 256x512, 16 x 512x1024, 16 x 384x1536, seeds 100..147):
+    the autotuner's choice over every launch shape on `tune_steps`-step trials, then each
+    launch shape (one launch per step, one persistent launch) at its best tile height,
+    captured as one CUDA graph of `steps` steps from the initial state and timed on one
+    replay."""
     lats = W.ensemble_48()
     Ls = []
     for lat in lats:
@@ -266,31 +320,36 @@ def bench_ensemble(torch, lbm, prec, steps, stream):
         L.init_from(lat)
         Ls.append(L)
     ens = lbm.Ensemble(Ls)
-    tuned = ens.tune(steps=2)
-    for L, lat in zip(Ls, lats):        # the trials advanced the state: start again
-        L.init_from(lat)
-    ens.capture(steps)
-    ens.graph_launch()                  # warm-up replay
-    ens.sync()
-    for L, lat in zip(Ls, lats):
-        L.init_from(lat)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ens.graph_launch()
-    e1.record(stream)
-    e1.synchronize()
-    ens.sync()
-    ms = e0.elapsed_time(e1)
+    tuned = ens.tune(steps=tune_steps)
     sites = sum(l.sites for l in lats)
-    mass = Ls[0].global_sums()[0]
+    bps = 2 * Q * BYTES_PER_POP[prec]
+    out = {"lattices": len(lats), "sites": sites, "steps": steps, "tuned": tuned,
+           "tuner_trial_steps": tune_steps, "graph": "one CUDA graph replay of all steps"}
+    for mode, key in ((0, "per_step_launches"), (1, "persistent_launch")):
+        ens.config(mode=mode, tile_z=128)
+        for L, lat in zip(Ls, lats):      # every timed run starts from the initial state
+            L.init_from(lat)
+        ens.step(2)                       # untimed warm-up (even: the lattices stay in their buffers)
+        ens.sync()
+        for L, lat in zip(Ls, lats):
+            L.init_from(lat)
+        ens.capture(steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.graph_launch()
+        e1.record(stream)
+        e1.synchronize()
+        ens.sync()
+        ms = e0.elapsed_time(e1)
+        mass = Ls[0].global_sums()[0]
+        out[key] = {"tile_z": 128, "ms_per_step": ms / steps, "mlups": sites * steps / (ms * 1e-3) / 1e6,
+                    "gbs": bps * sites * steps / (ms * 1e-3) / 1e9, "finite": bool(np.isfinite(mass))}
+    out["tuned_launch"] = "one persistent launch" if tuned["mode"] == 1 else "one launch per step"
     ens.close()
     for L in Ls:
         L.close()
-    bps = 2 * Q * BYTES_PER_POP[prec]
-    return {"lattices": len(lats), "sites": sites, "steps": steps, "ms_per_step": ms / steps,
-            "mlups": sites * steps / (ms * 1e-3) / 1e6, "gbs": bps * sites * steps / (ms * 1e-3) / 1e9,
-            "tuned": tuned, "finite": bool(np.isfinite(mass)), "launch": "one persistent launch" if tuned["mode"] == 1
-            else "one launch per step", "graph": "one CUDA graph replay"}
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_adjoint(torch):
@@ -494,23 +553,36 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
     L.init_from(lat)
-    L.step(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    e0.record(stream)
+    L.step(args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    warm_ms_step = e0.elapsed_time(e1) / args.warmup
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # The timed region (exactly K steps, a barrier and a device synchronisation on each side)
+    # is repeated R times so that the clock sampler covers it: R is set from the warm-up's
+    # step time (the same R on every rank) for about --clock-window seconds, at least 3; the
+    # reported time is the median repeat (max over ranks).
+    reps = repeats_for(warm_ms_step * args.steps, args.clock_window, ws)
+    rep_ms = []
     with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        L.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms_total, ms_step, mlups = aggregate_ranks(e0.elapsed_time(e1), args.steps, sites, ws, device="cuda")
+        clk.wait_first()
+        for _ in range(reps):
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            L.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            rep_ms.append(e0.elapsed_time(e1))
+    ms_total, ms_step, mlups = aggregate_ranks(statistics.median(rep_ms), args.steps, sites, ws, device="cuda")
     mass = L.global_sums()[0]
 
     # end to end through the C ABI with host buffers: every step copies its input state in
@@ -544,15 +616,15 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         extras["fp32_error_1024x2048"] = fp32_error(torch, lbm, lat, 500, stream)
         es = torch.cuda.Stream()           # graph capture needs a non-default stream
-        extras["ensemble_f64"] = bench_ensemble(torch, lbm, "f64_ff", 100, es)
-        extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", 100, es)
+        extras["ensemble_f64"] = bench_ensemble(torch, lbm, "f64_ff", W.ENSEMBLE_STEPS, es)
+        extras["ensemble_f32"] = bench_ensemble(torch, lbm, "f32", W.ENSEMBLE_STEPS, es)
         extras["adjoint"] = bench_adjoint(torch)
         extras["adjoint_kernel"] = bench_adjoint_kernel(torch, lbm, lat, 20, stream,
                                                         float(measured_peaks()[0].get("hbm_gbs", 6400.0)))
         extras["slabs"] = bench_slabs(torch, lbm, lat, 100, stream)
         extras["push_vs_pull"] = bench_push(torch, lbm, lat, 200, stream)
         extras["walls"] = bench_walls(torch, lbm, lat, 200, stream)
-        extras["large_lattice"] = bench_large(torch, lbm, 50, stream)
+        extras["precision_4096x8192"] = bench_precision(torch, lbm, W.PRECISION_STEPS, stream)
 
     if rank != 0:
         return
@@ -580,13 +652,20 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": ncu_traffic(KERNEL[prec], sites),
-                     "bytes_per_site": 2 * Q * BYTES_PER_POP[prec]},
+                     "bytes_per_site": 2 * Q * BYTES_PER_POP[prec],
+                     "spec_peak": SPEC_HBM_GBS, "frac_of_spec": achieved / SPEC_HBM_GBS,
+                     "target_frac": 0.70, "meets_target": bool(achieved / peak >= 0.70),
+                     "kernel": KERNEL[prec]},
         "e2e": ({"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                  "note": "lbm_step_host: per step host->device state, one step, device->host state (pinned; copies of consecutive steps overlapped)"}
                 if e2e_mlups is not None else
                 {"value": None, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                  "note": "lbm_step_host takes FP64 host buffers (FP64-storage contexts); not measured for this precision"}),
         "gpu_launches": args.steps,
+        "timed_repeats": {"count": len(rep_ms), "ms_per_step_min": min(rep_ms) / args.steps,
+                          "ms_per_step_median": statistics.median(rep_ms) / args.steps,
+                          "ms_per_step_max": max(rep_ms) / args.steps,
+                          "note": "each repeat is one timed region of exactly `steps` launches; value = median repeat"},
         "clocks": clk.summary(),
         "variants": variants,
         "mass_after": mass,
@@ -608,7 +687,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the ensemble, adjoint, slab, push, wall, large-lattice and FP32-error sections")
+                    help="skip the ensemble, adjoint, slab, push, wall, precision and FP32-error sections")
+    ap.add_argument("--clock-window", type=float, default=1.5,
+                    help="seconds of repeated timed regions the clock record must cover")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

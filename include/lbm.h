@@ -330,7 +330,10 @@ int lbm_ensemble_set_wait(lbm_ensemble *e, long long spin_limit_cycles, unsigned
  * share that array, so calls that may overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The first call on a device does
  * a one-time set-up (lattice constants, scratch address) with host synchronisation, so
- * make it before any stream capture.  Calls no cudaMalloc/cudaFree.  Asynchronous.    */
+ * make it before any stream capture.  The library keeps that set-up (here and for every
+ * context) for the life of the process: resetting a device's primary context
+ * (cudaDeviceReset) while the library is loaded is not supported.  Calls no
+ * cudaMalloc/cudaFree.  Asynchronous.                                                  */
 int lbm_row_mean_T_noalloc(const double *f, int Lx, int Lz, double *Tbar, void *cuda_stream);
 
 /* ---------------------------------------------------------------------------------

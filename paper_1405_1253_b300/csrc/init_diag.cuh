@@ -137,7 +137,7 @@ __global__ void k_moments(const typename S::T* __restrict__ f, int Lx, int Lz, d
 // Horizontal mean of T, stage 1: columns [c*nx_per, (c+1)*nx_per) summed into part[c][z].
 template <class S>
 __global__ void k_rowT_partial(const typename S::T* __restrict__ f, int Lx, int Lz, int nx_per,
-                               double* __restrict__ part) {
+                               double* __restrict__ part, int part_n) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (z >= Lz) return;
@@ -148,16 +148,16 @@ __global__ void k_rowT_partial(const typename S::T* __restrict__ f, int Lx, int 
         site_moments<S>(f, x, z, Lz, Lx * Lz, R, U, V, TT);
         s += TT;
     }
-    part[c * Lz + z] = s;
+    part[LBM_IDX(c * Lz + z, part_n)] = s;
 }
 
 // Stage 2: Tbar[z] = (sum_c part[c][z]) / Lx, chunks added in order.
-__global__ void k_rowT_final(const double* __restrict__ part, int nchunk, int Lx, int Lz,
+__global__ void k_rowT_final(const double* __restrict__ part, int part_n, int nchunk, int Lx, int Lz,
                              double* __restrict__ Tbar) {
     const int z = blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= Lz) return;
     double s = 0.0;
-    for (int c = 0; c < nchunk; c++) s += part[c * Lz + z];
+    for (int c = 0; c < nchunk; c++) s += part[LBM_IDX(c * Lz + z, part_n)];
     Tbar[z] = s / (double)Lx;
 }
 

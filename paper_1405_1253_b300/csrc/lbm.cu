@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -725,14 +726,15 @@ static int row_mean_device(lbm_ctx* c, double* Tbar_dev) {
     if (rc) return rc;
     dim3 grid((c->Lz + 127) / 128, nch);
     const void* f = c->buf[c->cur];
+    const int part_n = (int)std::min(c->part_cap, (size_t)INT_MAX);
     switch (c->prec) {
         case LBM_F64: case LBM_F64_FF:
-            k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, nx_per, c->part); break;
+            k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, nx_per, c->part, part_n); break;
         default:
-            k_rowT_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, c->Lx, c->Lz, nx_per, c->part); break;
+            k_rowT_partial<StoreF32><<<grid, 128, 0, c->stream>>>((const float*)f, c->Lx, c->Lz, nx_per, c->part, part_n); break;
     }
     LAUNCH_CHECK();
-    k_rowT_final<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->part, nch, c->Lx, c->Lz, Tbar_dev);
+    k_rowT_final<<<(c->Lz + 127) / 128, 128, 0, c->stream>>>(c->part, part_n, nch, c->Lx, c->Lz, Tbar_dev);
     LAUNCH_CHECK();
     return LBM_OK;
 }
@@ -1354,9 +1356,9 @@ extern "C" int lbm_row_mean_T_noalloc(const double* f, int Lx, int Lz, double* T
     const int nch = (Lx + nx_per - 1) / nx_per;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     dim3 grid((Lz + 127) / 128, nch);
-    k_rowT_partial<StoreF64><<<grid, 128, 0, st>>>(f, Lx, Lz, nx_per, scratch);
+    k_rowT_partial<StoreF64><<<grid, 128, 0, st>>>(f, Lx, Lz, nx_per, scratch, LBM_NOALLOC_SCRATCH_DOUBLES);
     LAUNCH_CHECK();
-    k_rowT_final<<<(Lz + 127) / 128, 128, 0, st>>>(scratch, nch, Lx, Lz, Tbar);
+    k_rowT_final<<<(Lz + 127) / 128, 128, 0, st>>>(scratch, LBM_NOALLOC_SCRATCH_DOUBLES, nch, Lx, Lz, Tbar);
     LAUNCH_CHECK();
     return LBM_OK;
 }

@@ -23,7 +23,9 @@ def _rank(rank, world, port, q):
     import bench
     ms_local = [100.0, 250.0][rank]
     res = bench.aggregate_ranks(ms_local, steps=50, sites_per_rank=1000, world_size=world, device="cpu")
-    q.put((rank, res))
+    # each rank's own estimate of the timed region differs; every rank must run the same count
+    reps = bench.repeats_for([10.0, 2.0][rank], 1.0, world, device="cpu")
+    q.put((rank, (res, reps)))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -40,7 +42,8 @@ def test_aggregate_over_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     for rank in (0, 1):
-        ms_total, ms_step, mlups = out[rank]
+        (ms_total, ms_step, mlups), reps = out[rank]
+        assert reps == 500                            # the larger of 100 and 500 repeats
         assert ms_total == 250.0                      # max over ranks
         assert ms_step == 5.0
         assert mlups == pytest.approx(2 * 1000 / 5e-3 / 1e6)
@@ -49,6 +52,15 @@ def test_aggregate_over_two_gloo_ranks():
 def test_single_rank_needs_no_collective():
     import bench
     assert bench.aggregate_ranks(80.0, 40, 2000, 1) == (80.0, 2.0, 2000 / 2e-3 / 1e6)
+
+
+def test_timed_region_repeats_cover_the_clock_window():
+    """A short timed region (20 steps of ~0.28 ms) is repeated to cover the clock window; a
+    long one still runs at least three times, and the count is capped."""
+    import bench
+    assert bench.repeats_for(5.6, 1.5, 1) == 268
+    assert bench.repeats_for(560.0, 1.5, 1) == 3
+    assert bench.repeats_for(1e-4, 1.5, 1) == 2000
 
 
 def _reference_line(monkeypatch, capsys, steps, warmup, rank="0"):

@@ -1,6 +1,6 @@
 """The bounds-checked build (liblbm_checked.so, every population load and store index-checked):
 a child process running every kernel path — pull and push steps in every precision on edge
-shapes, propagate, moments and row statistics, the slabs, the ensemble in both launch modes,
+shapes, propagate, moments and row statistics, the allocation-free row mean, the slabs, the ensemble in both launch modes,
 the adjoint, thermal walls, host stepping — must meet no out-of-range index."""
 import os
 import subprocess
@@ -27,6 +27,10 @@ def exercise():
             L.row_stats()
             L.tent_widths(lat.T_u, lat.T_m, lat.T_d)
             L.populations()
+            if prec != "f32":                     # the allocation-free row mean (FP64 arrays)
+                Tb = torch.empty(Lz, dtype=torch.float64, device="cuda")
+                lbm.row_mean_T_noalloc(L.current().data_ptr(), Lx, Lz, Tb.data_ptr(),
+                                       L.stream.cuda_stream)
     lat = W.Lattice(48, 70, tau=0.8, grav=1e-4, K=4, sigma=1.0, seed=22)
     for prec in ("f64_ff", "f32"):
         Ls = []

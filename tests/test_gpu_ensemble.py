@@ -1,10 +1,13 @@
 """The ensemble runner: uneven lattices advanced together (per-step launches, one
-persistent launch, a captured CUDA graph) give exactly the states of each lattice
-stepped alone; the persistent launch's bounded barrier wait ends with LBM_ETIMEOUT
-instead of hanging when its target can never be met."""
+persistent launch, a captured CUDA graph) match the FP64 oracle stepping each lattice
+alone (to 1e-13 for the float-float collide, within the stated FP32 field bound for FP32
+storage) and give exactly the states of each lattice stepped alone on the GPU; the
+persistent launch's bounded barrier wait ends with LBM_ETIMEOUT instead of hanging when
+its target can never be met."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1405_1253_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -19,14 +22,64 @@ def env():
     return torch, lbm
 
 
+def lattices():
+    return [W.Lattice(lx, lz, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=300 + i)
+            for i, (lx, lz) in enumerate(SHAPES)]
+
+
 def make_set(lbm, prec, stream):
     Ls = []
-    for i, (lx, lz) in enumerate(SHAPES):
-        lat = W.Lattice(lx, lz, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=300 + i)
-        L = lbm.Lattice(lx, lz, lat.tau, lat.grav, prec=prec, stream=stream)
+    for lat in lattices():
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
         L.init_from(lat)
         Ls.append(L)
     return Ls
+
+
+def check_against_oracle(L, lat, prec, nsteps):
+    """The lattice after nsteps against the oracle's nsteps from its own initial state."""
+    ref = oracle.step(oracle.init_layers(lat.Lx, lat.Lz, **lat.layer_args()), lat.tau, lat.grav, nsteps)
+    if prec == "f32":
+        rho32, _, _, T32 = L.moments()
+        rho, _, _, T = oracle.moments(ref, lat.grav)
+        assert np.linalg.norm(rho32 - rho) / np.linalg.norm(rho) < 1e-5
+        assert np.linalg.norm(T32 - T) / np.linalg.norm(T) < 1e-5
+    else:
+        got = L.populations()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["f64_ff", "f32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ensemble_matches_oracle(env, prec, mode):
+    torch, lbm = env
+    stream = torch.cuda.Stream()
+    ens_l = make_set(lbm, prec, stream)
+    ens = lbm.Ensemble(ens_l)
+    ens.config(mode=mode, tile_z=128)
+    ens.step(3)
+    ens.step(4)
+    ens.sync()
+    for L, lat in zip(ens_l, lattices()):
+        check_against_oracle(L, lat, prec, 7)
+    ens.close()
+
+
+@pytest.mark.parametrize("prec", ["f64_ff", "f32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ensemble_graph_replay_matches_oracle(env, prec, mode):
+    torch, lbm = env
+    stream = torch.cuda.Stream()
+    ens_l = make_set(lbm, prec, stream)
+    ens = lbm.Ensemble(ens_l)
+    ens.config(mode=mode, tile_z=128)
+    ens.capture(4)
+    for _ in range(3):
+        ens.graph_launch()
+    ens.sync()
+    for L, lat in zip(ens_l, lattices()):
+        check_against_oracle(L, lat, prec, 12)
+    ens.close()
 
 
 @pytest.mark.parametrize("prec", ["f64_ff", "f32"])

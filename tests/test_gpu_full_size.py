@@ -35,6 +35,26 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
+@pytest.mark.parametrize("lat", [W.THROUGHPUT_1024x2048, W.PRECISION_4096x8192], ids=["1024x2048", "4096x8192"])
+def test_init_full_size_sampled_columns(env, lat):
+    """The initial state of the throughput (64 modes) and precision (128 modes) lattices
+    against the oracle's, column by column: the mode sums at every phase of the largest
+    wavenumbers, the tanh and hydrostatic profiles and the pressure continuity over the
+    full height.  Columns are cut on the device."""
+    torch, lbm = env
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64_ff")
+    L.init_from(lat)
+    f = L.current()
+    cols = [0, 1, lat.Lx // 3, lat.Lx // 2 + 7, lat.Lx - 1]
+    ref = oracle.init_columns(lat.Lx, lat.Lz, cols, **lat.layer_args())
+    for j, x0 in enumerate(cols):
+        got = column(torch, f, lat.Lx, lat.Lz, x0)
+        assert np.max(np.abs(got - ref[:, j, :]) / np.abs(ref[:, j, :])) < 1e-13
+    del f
+    L.close()
+    torch.cuda.empty_cache()
+
+
 def test_largest_configuration_4096x8192_sampled_columns(env):
     """The precision configuration (4096 x 8192, 19.9 GB for the two copies): 2 float-float
     steps against the oracle on 13-column windows (the centre column depends on +-6)."""
@@ -98,3 +118,35 @@ def test_thermal_walls_full_size_sampled_columns(env):
                           walls=(lat.T_d, lat.T_u))[:, 12, :]
         assert np.max(np.abs(column(torch, f2, lat.Lx, lat.Lz, x0) - ref) / np.abs(ref)) < 1e-13
     L.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ensemble_48_lattices_sampled_columns(env, mode):
+    """The batching configuration (48 uneven lattices, 19.9 M sites) in one ensemble, in each
+    launch shape, under a captured graph of 2 steps: sampled columns of lattices of every
+    size against the oracle's 2 steps from its own initial state on a 13-column window."""
+    torch, lbm = env
+    lats = W.ensemble_48()
+    stream = torch.cuda.Stream()
+    Ls = []
+    for lat in lats:
+        L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64_ff", stream=stream)
+        L.init_from(lat)
+        Ls.append(L)
+    ens = lbm.Ensemble(Ls)
+    ens.config(mode=mode, tile_z=128)
+    ens.capture(2)
+    ens.graph_launch()
+    ens.sync()
+    for i, x0 in ((0, 0), (15, 255), (16, 100), (31, 511), (32, 3), (47, 383)):
+        lat, L = lats[i], Ls[i]
+        cols = [x0 + k for k in range(-6, 7)]
+        win = oracle.init_columns(lat.Lx, lat.Lz, cols, **lat.layer_args())
+        ref = oracle.step(win, lat.tau, lat.grav, 2)[:, 6, :]
+        got = column(torch, L.current(), lat.Lx, lat.Lz, x0)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-13, (i, x0)
+    ens.close()
+    for L in Ls:
+        L.close()
+    del Ls
+    torch.cuda.empty_cache()

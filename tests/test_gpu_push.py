@@ -1,7 +1,9 @@
-"""Push form of the step against the pull form (Sec. III.B): push steps from P f equal P
-applied to the pull steps from f, bit for bit for the float-float and FP32 collides (to a few
-ulps for the native FP64 one), on edge shapes (x wrap at Lx < 3, ragged z tails, lattices that
-are all wall rows); P itself (lbm_propagate) equals the oracle's propagate + bc."""
+"""Push form of the step (Sec. III.B): push steps from P f match P applied to the oracle's
+steps from f (1e-13 for the FP64-accurate collides, the stated FP32 field bound for FP32
+storage), with P f formed by the oracle's propagate + bc; push steps from P f equal P applied
+to the pull steps from f, bit for bit for the float-float and FP32 collides (to a few ulps for
+the native FP64 one), on edge shapes (x wrap at Lx < 3, ragged z tails, lattices that are all
+wall rows); P itself (lbm_propagate) equals the oracle's propagate + bc."""
 import numpy as np
 import pytest
 
@@ -37,6 +39,29 @@ def test_push_equals_propagated_pull(lbm, prec, Lx, Lz):
         np.testing.assert_allclose(got, ref, rtol=1e-13, atol=0)
     else:
         assert np.array_equal(got, ref)
+
+
+def oracle_P(f):
+    return oracle.bc(f, oracle.propagate(f))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64_ff", "f32"])
+@pytest.mark.parametrize("Lx,Lz", [(1, 6), (2, 8), (5, 131), (16, 70), (64, 128)])
+def test_push_matches_oracle(lbm, prec, Lx, Lz):
+    lat = W.Lattice(Lx, Lz, tau=0.8, grav=2e-4, K=2, sigma=0.5, seed=11)
+    f0 = oracle.init_layers(Lx, Lz, **lat.layer_args())
+    ref = oracle_P(oracle.step(f0, lat.tau, lat.grav, 6))
+    B = lbm.Lattice(Lx, Lz, lat.tau, lat.grav, prec=prec)
+    B.set_populations(oracle_P(f0))
+    B.step_push(6)
+    if prec == "f32":
+        rho32, _, _, T32 = B.moments()
+        rho, _, _, T = oracle.moments(ref, lat.grav)
+        assert np.linalg.norm(rho32 - rho) / np.linalg.norm(rho) < 1e-5
+        assert np.linalg.norm(T32 - T) / np.linalg.norm(T) < 1e-5
+    else:
+        got = B.populations()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-13
 
 
 @pytest.mark.parametrize("Lx,Lz", [(1, 6), (3, 37), (12, 48)])
