@@ -40,6 +40,7 @@ struct AdjParamsFF {
     ff3 r_24, inv24;       // r / 24, 1 / 24
     ff c6[NSHELL];         // r^2 |c|^2 - 6 of each shell
     ff c4[NSHELL];         // 2 (r^2 |c|^2 - 4)
+    int off[Q];            // pull offsets (pull_offsets) for the columns off the periodic seam
 };
 
 // a * c, not renormalised.
@@ -63,11 +64,7 @@ __device__ __forceinline__ ff ff_add_big_u_x2(ff a, ff b) {
 __device__ __forceinline__ ff ff_renorm2(ff a) { return two_sum(a.hi, a.lo); }
 
 // Packed two-lane forms of the adjoint's float-float operations (lane-wise the operations of
-// the scalar functions, so the results are the same bits).
-__device__ __forceinline__ ffx2 ffx2_add_u(const ffx2& a, const ffx2& b) {            // ff_add_u
-    const ffx2 s = ffx2_two_sum(a.hi, b.hi);
-    return ffx2{s.hi, x2_add(s.lo, x2_add(a.lo, b.lo))};
-}
+// the scalar functions, so the results are the same bits; ffx2_add_u is in ff.cuh).
 __device__ __forceinline__ ffx2 ffx2_sub_u(const ffx2& a, const ffx2& b) {            // ff_add_u(a, ff_neg(b))
     const f32x2 s = x2_sub(a.hi, b.hi), bb = x2_sub(s, a.hi);
     const f32x2 e = x2_sub(x2_sub(a.hi, x2_sub(s, bb)), x2_add(b.hi, bb));
@@ -81,6 +78,16 @@ __device__ __forceinline__ ffx2 ffx2_mul_c3_u(const ffx2& a, const ff3& c) {    
     e0 = fmaf(a0, c.lo, e0);  e1 = fmaf(a1, c.lo, e1);
     e0 = fmaf(x2_lane0(a.lo), c.hi, e0); e1 = fmaf(x2_lane1(a.lo), c.hi, e1);
     return ffx2{p, x2_pack(e0, e1)};
+}
+// ff_mul_c3_u with the constant c0 in lane 0 and c1 in lane 1
+__device__ __forceinline__ ffx2 ffx2_mul_c3_u2(const ffx2& a, const ff3& c0, const ff3& c1) {
+    const f32x2 chi = x2_pack(c0.hi, c1.hi);
+    const f32x2 p = x2_mul(a.hi, chi);
+    f32x2 e = x2_prod_err(a.hi, chi, p);
+    e = x2_fma(a.hi, x2_pack(c0.lo2, c1.lo2), e);
+    e = x2_fma(a.hi, x2_pack(c0.lo, c1.lo), e);
+    e = x2_fma(a.lo, chi, e);
+    return ffx2{p, e};
 }
 __device__ __forceinline__ ffx2 ffx2_add_big_u_x2(const ffx2& a, const ffx2& b) {     // ff_add_big_u_x2
     const f32x2 two = x2_pack(2.0f, 2.0f);
@@ -159,19 +166,20 @@ template <bool WALL>
 struct DstSource {
     double* __restrict__ out;
     const SiteAddr& ad;
-    const int* sbase;
+    const int* sbase;     // as SrcGlobal: the tile's pull bases or the offsets
+    int zoff;             // the row z, or the site x Lz + z with the offsets
     template <int L>
     __device__ __forceinline__ void put(double v) const {
         if constexpr (WALL) out[LBM_IDX((ad.template src<L, true>()), Q * ad.plane)] = v;
-        else out[LBM_IDX(sbase[L] + ad.z, Q * ad.plane)] = v;
+        else out[LBM_IDX(sbase[L] + zoff, Q * ad.plane)] = v;
     }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
         if constexpr (WALL) {
             out[LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane)] = va;
             out[LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane)] = vb;
         } else {
-            out[LBM_IDX(sbase[pi.A] + ad.z, Q * ad.plane)] = va;
-            out[LBM_IDX(sbase[pi.B] + ad.z, Q * ad.plane)] = vb;
+            out[LBM_IDX(sbase[pi.A] + zoff, Q * ad.plane)] = va;
+            out[LBM_IDX(sbase[pi.B] + zoff, Q * ad.plane)] = vb;
         }
     }
 };
@@ -225,12 +233,18 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
     const ff th2 = ff_mul(th, th), thu2 = ff_mul(th, u2), u4 = ff_mul_u(u2, u2);
     const ff k00 = ff_add(ff_add(ff_make(24.0f, 0.0f), ff_mul_f_u(u2, -12.0f)),
                           ff_add(ff_mul_f_u(u4, 3.0f), ff_mul_f_u(ff_add(thu2, ff_sub(th2, th)), 24.0f)));
-    const ff k01 = ff_mul_c3(ff_sub(ff_mul_pow2(th, 2.0f), ff_add(thu2, ff_mul_pow2(th2, 4.0f))), ff3_of(d_lat.r2x6));
-    const ff k02 = ff_mul_c3(th2, ff3_of(d_lat.r4x3));
-    const ff k10 = ff_add(ff_make(24.0f, 0.0f), ff_add(ff_mul_f_u(u2, -12.0f), ff_mul_f_u(th, -48.0f)));
+    // (k01, k02) and (k10, k20) in the lanes of packed registers, and k21 = k11 / 2 exactly,
+    // as in collide_ff
+    const ff k01v = ff_sub(ff_mul_pow2(th, 2.0f), ff_add(thu2, ff_mul_pow2(th2, 4.0f)));
+    const ffx2 k012 = ffx2_mul_c3(ffx2{x2_pack(k01v.hi, th2.hi), x2_pack(k01v.lo, th2.lo)},
+                                  ff3_of(d_lat.r2x6), ff3_of(d_lat.r4x3));
+    const ff k01 = ffx2_lane0(k012), k02 = ffx2_lane1(k012);
+    const ffx2 k1020 = ffx2_add(ffx2{x2_pack(24.0f, 12.0f), x2_pack(0.0f, 0.0f)},
+                                ffx2_add(ffx2_mul_f_u(ffx2_both(u2), x2_pack(-12.0f, -6.0f)),
+                                         ffx2_mul_f_u(ffx2_both(th), x2_pack(-48.0f, -36.0f))));
+    const ff k10 = ffx2_lane0(k1020), k20 = ffx2_lane1(k1020);
     const ff k11 = ff_mul_c3(th, ff3_of(d_lat.r2x12));
-    const ff k20 = ff_add(ff_make(12.0f, 0.0f), ff_add(ff_mul_f_u(u2, -6.0f), ff_mul_f_u(th, -36.0f)));
-    const ff k21 = ff_mul_c3(th, ff3_of(d_lat.r2x6));
+    const ff k21 = ff_mul_pow2(k11, 0.5f);
     // 4 H0 = (-4 + 4 u2 + 8 th) + r^2 (2 - u2 - 8 th) |c|^2 + r^4 th |c|^4
     const ff h00 = ff_add(ff_make(-4.0f, 0.0f), ff_add(ff_mul_pow2(u2, 4.0f), ff_mul_pow2(th, 8.0f)));
     const ff h01 = ff_mul_c3(ff_sub(ff_make(2.0f, 0.0f), ff_add(u2, ff_mul_pow2(th, 8.0f))), p.r2);
@@ -248,10 +262,11 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         sm.Bz = ff_make(0.0f, 0.0f);
     }
     // the two pairs of each iteration in the lanes of packed FP32 registers; each lane's terms
-    // are added to the scalar sums in pair order, as the scalar loop does
+    // are added to the sums, lane 0 first (separate sums per lane need registers that the
+    // 96-register budget does not have: measured 3% slower)
     const ffx2 A2 = ffx2_both(a), B2 = ffx2_both(b);
     auto pair2_sums = [&](const PairInfo& p0, const PairInfo& p1, const ffx2& K0, const ffx2& K1, const ffx2& K2,
-                          const ffx2& H, const ff3& W, const ffx2& c6, const ffx2& c4) {
+                          const ffx2& H, const ff3& W0, const ff3& W1, const ffx2& c6, const ffx2& c4) {
         double v0a, v0b, v1a, v1b;
         lsrc.pair(p0, v0a, v0b);
         lsrc.pair(p1, v1a, v1b);
@@ -261,8 +276,8 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         const ff lb1 = bits_to_ff_scaled((uint32_t)__double2hiint(v1b), (uint32_t)__double2loint(v1b), S);
         const ffx2 la{x2_pack(la0.hi, la1.hi), x2_pack(la0.lo, la1.lo)};
         const ffx2 lb{x2_pack(lb0.hi, lb1.hi), x2_pack(lb0.lo, lb1.lo)};
-        const ffx2 ls = ffx2_mul_c3_u(ffx2_add_u(la, lb), W);
-        const ffx2 ld = ffx2_mul_c3_u(ffx2_sub_u(la, lb), W);
+        const ffx2 ls = ffx2_mul_c3_u2(ffx2_add_u(la, lb), W0, W1);
+        const ffx2 ld = ffx2_mul_c3_u2(ffx2_sub_u(la, lb), W0, W1);
         const f32x2 fcx = x2_pack(p0.fcx, p1.fcx), fcz = x2_pack(p0.fcz, p1.fcz);
         const ffx2 sx = ffx2_mul_f_u(A2, fcx), sz = ffx2_mul_f_u(B2, fcz);
         const ffx2 st = ffx2_two_sum(sx.hi, sz.hi);
@@ -290,25 +305,32 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
         sm.U = ff_add_u(sm.U, ffx2_lane1(tU));
         sm.C = ff_add_u(sm.C, ffx2_lane1(tC));
     };
+    // shells in the groups of d_groups (step_ff.cuh): the coefficients of two shells are formed
+    // together, one shell per lane, and each iteration takes one pair of each
+    const ffx2 k00b = ffx2_both(k00), k01b = ffx2_both(k01), k02b = ffx2_both(k02);
+    const ffx2 k10b = ffx2_both(k10), k11b = ffx2_both(k11), k20b = ffx2_both(k20), k21b = ffx2_both(k21);
+    const ffx2 h00b = ffx2_both(h00), h01b = ffx2_both(h01), h02b = ffx2_both(h02);
 #pragma unroll 1
-    for (int sh = 1; sh < NSHELL; sh++) {
-        const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
-        const float C2 = d_pairs[k0].fc2;
-        const ff K0 = ff_add_u(k00, ff_mul_f_u(ff_add_u(k01, ff_mul_f_u(k02, C2)), C2));
-        const ff K1 = ff_add_u(k10, ff_mul_f_u(k11, C2));
-        const ff K2 = ff_add_u(k20, ff_mul_f_u(k21, C2));
-        const ff H = ff_add_u(h00, ff_mul_f_u(ff_add_u(h01, ff_mul_f_u(h02, C2)), C2));
-        const ffx2 K0b = ffx2_both(K0), K1b = ffx2_both(K1), K2b = ffx2_both(K2), Hb = ffx2_both(H);
-        const ffx2 c6 = ffx2_both(p.c6[sh]), c4 = ffx2_both(p.c4[sh]);
+    for (int g = 0; g < NGROUP; g++) {
+        const ShellGroup sg = d_groups[g];
+        const f32x2 C2 = x2_pack(sg.c2a, sg.c2b);
+        const ffx2 K0 = ffx2_add_u(k00b, ffx2_mul_f_u(ffx2_add_u(k01b, ffx2_mul_f_u(k02b, C2)), C2));
+        const ffx2 K1 = ffx2_add_u(k10b, ffx2_mul_f_u(k11b, C2));
+        const ffx2 K2 = ffx2_add_u(k20b, ffx2_mul_f_u(k21b, C2));
+        const ffx2 H = ffx2_add_u(h00b, ffx2_mul_f_u(ffx2_add_u(h01b, ffx2_mul_f_u(h02b, C2)), C2));
+        const ff c6a = p.c6[sg.sa], c6b = p.c6[sg.sb], c4a = p.c4[sg.sa], c4b = p.c4[sg.sb];
+        const ffx2 c6{x2_pack(c6a.hi, c6b.hi), x2_pack(c6a.lo, c6b.lo)};
+        const ffx2 c4{x2_pack(c4a.hi, c4b.hi), x2_pack(c4a.lo, c4b.lo)};
 #pragma unroll 1
-        for (int k = k0; k < k1; k += 2)
-            pair2_sums(d_pairs[k], d_pairs[k + 1], K0b, K1b, K2b, Hb, p.wsh[sh], c6, c4);
+        for (int k = 0; k < sg.n; k++)
+            pair2_sums(d_pairs[sg.k0 + k], d_pairs[sg.k1 + k], K0, K1, K2, H, p.wsh[sg.sa], p.wsh[sg.sb], c6, c4);
     }
+    const ff sA = sm.A, sBx = sm.Bx, sBz = sm.Bz, sU = sm.U, sC = sm.C;
     // -- A', B', C' (times omega, in units of the block exponent) ---------------------------
-    const ff A = ff_mul_c3(ff_renorm2(sm.A), p.inv24);
-    const ff Bx = ff_mul_c3(ff_renorm2(sm.Bx), p.r_24), Bz = ff_mul_c3(ff_renorm2(sm.Bz), p.r_24);
-    const ff Bu = ff_mul_pow2(ff_mul_c3(ff_renorm2(sm.U), p.inv24), -0.5f);
-    const ff Cs = ff_mul_pow2(ff_renorm2(sm.C), 0.25f);
+    const ff A = ff_mul_c3(ff_renorm2(sA), p.inv24);
+    const ff Bx = ff_mul_c3(ff_renorm2(sBx), p.r_24), Bz = ff_mul_c3(ff_renorm2(sBz), p.r_24);
+    const ff Bu = ff_mul_pow2(ff_mul_c3(ff_renorm2(sU), p.inv24), -0.5f);
+    const ff Cs = ff_mul_pow2(ff_renorm2(sC), 0.25f);
     const ff Btx = ff_add(Bx, ff_mul_pow2(ff_mul(Bu, ux), 2.0f));
     const ff Btz = ff_add(Bz, ff_mul_pow2(ff_mul(Bu, usz), 2.0f));
     // |u|^2 / 2 - T with T = 1 + tm1
@@ -326,13 +348,17 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
     // even part A' + C'|xi|^2 once per shell, odd part B'.xi once per pair, each rounded to
     // binary64; the sum and the relaxation are FP64 (the FP64 pipe has room for the adds,
     // the issue slots of a float-float add and a second assembly per population it saves)
+    const ffx2 APb = ffx2_both(Ap), PH2 = ffx2_both(ph2);
 #pragma unroll 1
-    for (int sh = 1; sh < NSHELL; sh++) {
-        const int k0 = d_shell_first[sh], k1 = k0 + d_shell_npair[sh];
-        const double ev = ff_to_double_scaled(ff_renorm2(ff_add_u(Ap, ff_mul_f_u(ph2, d_pairs[k0].fc2))), S);
+    for (int g = 0; g < NGROUP; g++) {
+        const ShellGroup sg = d_groups[g];
+        // A' + C'|xi|^2 of the two shells of the group (lanes 0, 1)
+        const ffx2 e2 = ffx2_add_u(APb, ffx2_mul_f_u(PH2, x2_pack(sg.c2a, sg.c2b)));
+        const ffx2 er = ffx2_two_sum(e2.hi, e2.lo);                                      // ff_renorm2
+        const double eva = ff_to_double_scaled(ffx2_lane0(er), S), evb = ff_to_double_scaled(ffx2_lane1(er), S);
 #pragma unroll 1
-        for (int k = k0; k < k1; k += 2) {
-            const PairInfo p0 = d_pairs[k], p1 = d_pairs[k + 1];
+        for (int k = 0; k < sg.n; k++) {
+            const PairInfo p0 = d_pairs[sg.k0 + k], p1 = d_pairs[sg.k1 + k];
             double v0a, v0b, v1a, v1b;
             lsrc.template pair<true>(p0, v0a, v0b);
             lsrc.template pair<true>(p1, v1a, v1b);
@@ -341,8 +367,8 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
             const ffx2 ot = ffx2_two_sum(ox.hi, oz.hi);
             const ffx2 o = ffx2_two_sum(ot.hi, x2_add(ot.lo, x2_add(ox.lo, oz.lo)));     // ff_renorm2
             const double od0 = ff_to_double_scaled(ffx2_lane0(o), S), od1 = ff_to_double_scaled(ffx2_lane1(o), S);
-            dst.pair(p0, fma(p.one_m_omega_d, v0a, ev + od0), fma(p.one_m_omega_d, v0b, ev - od0));
-            dst.pair(p1, fma(p.one_m_omega_d, v1a, ev + od1), fma(p.one_m_omega_d, v1b, ev - od1));
+            dst.pair(p0, fma(p.one_m_omega_d, v0a, eva + od0), fma(p.one_m_omega_d, v0b, eva - od0));
+            dst.pair(p1, fma(p.one_m_omega_d, v1a, evb + od1), fma(p.one_m_omega_d, v1b, evb - od1));
         }
     }
 }
@@ -350,7 +376,8 @@ __device__ __forceinline__ void adjoint_site_ff(const MSRC& msrc, const LamOwn& 
 // One tile b of the tiling t (the step's tiling: wall tiles, then interior columns); the
 // moments come from f_t (ft) or, if ft is null, from the record mom.
 // PDL: launched with launch_pdl (every thread waits for the previous grid before its first
-// global access, as tile_ff).
+// global access, as tile_ff).  Interior tiles off the periodic seam take their pull sources
+// and scatter targets from p.off (p a __grid_constant__ kernel parameter), as tile_ff.
 template <bool PDL = false>
 __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, const int64_t* __restrict__ mom,
                                                 const double* __restrict__ lam_next, double* __restrict__ lam_out,
@@ -362,27 +389,39 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
         if constexpr (PDL) pdl_wait();
         if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
         const LamOwn lsrc{lam_next, ad.dst(), p.plane};
-        const DstSource<true> dst{lam_out, ad, sbase};
+        const DstSource<true> dst{lam_out, ad, sbase, 0};
         if (mom) {
             adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
         } else {
-            const SrcGlobal<true, LoadNC> src{ft, ad, sbase};
+            const SrcGlobal<true, LoadNC> src{ft, ad, sbase, 0};
             adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC>>{src}, lsrc, dst, p);
         }
         return;
     }
-    fill_pull_bases(sbase, tile_column(t, b), p.Lx, p.Lz, p.plane);
+    // an interior tile's sources and targets: through the offsets or the tile's table (two
+    // instances of the site code, so that each reads its bases from a known memory space)
+    auto interior = [&](const int* bases, int zoff) {
+        const LamOwn lsrc{lam_next, ad.dst(), p.plane};
+        const DstSource<false> dst{lam_out, ad, bases, zoff};
+        if (mom) {
+            adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
+        } else {
+            const SrcGlobal<false, LoadNC> src{ft, ad, bases, zoff};
+            adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, dst, p);
+        }
+    };
+    const int x = tile_column(t, b);
+    if (off_seam(x, p.Lx)) {                        // block-uniform
+        if constexpr (PDL) pdl_wait();
+        if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
+        interior(p.off, ad.dst());
+        return;
+    }
+    fill_pull_bases(sbase, x, p.Lx, p.Lz, p.plane);
     __syncthreads();
     if constexpr (PDL) pdl_wait();
     if (!ad.setup(p.Lx, p.Lz, p.plane, t, b, wall)) return;
-    const LamOwn lsrc{lam_next, ad.dst(), p.plane};
-    const DstSource<false> dst{lam_out, ad, sbase};
-    if (mom) {
-        adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
-    } else {
-        const SrcGlobal<false, LoadNC> src{ft, ad, sbase};
-        adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, dst, p);
-    }
+    interior(sbase, ad.z);
 }
 
 // Two register budgets: 5 resident blocks per SM (96 registers, 20 warps; 4.6% faster than 4
@@ -392,7 +431,7 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
 template <int MINB>
 __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next, double* __restrict__ lam_out,
-             AdjParamsFF p, Tiling t) {
+             const __grid_constant__ AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
     pdl_allow_next();
     adjoint_tile_ff<true>(ft, nullptr, lam_next, lam_out, p, t, blockIdx.x, sbase);
@@ -402,7 +441,7 @@ k_adjoint_ff(const double* __restrict__ ft, const double* __restrict__ lam_next,
 template <int MINB>
 __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff_moments(const int64_t* __restrict__ mom, const double* __restrict__ lam_next,
-                     double* __restrict__ lam_out, AdjParamsFF p, Tiling t) {
+                     double* __restrict__ lam_out, const __grid_constant__ AdjParamsFF p, Tiling t) {
     __shared__ int sbase[Q];
     pdl_allow_next();
     adjoint_tile_ff<true>(nullptr, mom, lam_next, lam_out, p, t, blockIdx.x, sbase);
@@ -451,6 +490,7 @@ inline AdjParamsFF adj_ff_params(const StepParams& p, const double* w_shell, dou
     }
     q.us_z = ff_host(p.us_z);
     q.T_shift = ff_host(p.T_shift);
+    pull_offsets(p.Lz, p.plane, q.off);
     q.r2 = ff3_host(r2);
     q.r4 = ff3_host(r2 * r2);
     q.r_24 = ff3_host(rl / 24.0L);

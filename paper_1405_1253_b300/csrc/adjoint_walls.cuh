@@ -53,7 +53,7 @@ struct DstSourceThermal {
 template <int MINB>
 __global__ void __launch_bounds__(BLOCK_Z, MINB)
 k_adjoint_ff_thermal(const double* __restrict__ ft, const double* __restrict__ lam_next,
-                     double* __restrict__ lam_out, AdjParamsFF p, Tiling t, ThermalWall w,
+                     double* __restrict__ lam_out, const __grid_constant__ AdjParamsFF p, Tiling t, ThermalWall w,
                      double* __restrict__ gmu) {
     __shared__ int sbase[Q];
     __shared__ double s_out[2][WALL_COLS];

@@ -22,6 +22,17 @@ __constant__ int d_shell_first[8];
 __constant__ int d_shell_npair[8];
 __constant__ int d_vel[37][2];
 
+// The seven moving shells in four groups whose coefficients a collide forms together, one
+// shell per lane of packed FP32 registers: (|c|^2 = 1, 2), (4, 8), (5, 10) pair shells with
+// equal pair counts, lane 0 taking pairs k0 .. k0 + n - 1 of shell sa and lane 1 pairs
+// k1 .. k1 + n - 1 of shell sb; the last group is shell 9 alone, its two pairs one per lane.
+struct ShellGroup {
+    int k0, k1, n, sa, sb;
+    float c2a, c2b;          // |c|^2 of the two lanes' shells
+};
+constexpr int NGROUP = 4;
+__constant__ ShellGroup d_groups[NGROUP];
+
 // Bounds-checked builds (-DLBM_BOUNDS_CHECK): LBM_IDX(i, n) tests every population index
 // against the element count n of its buffer; an index outside [0, n) is counted in
 // g_oob_count and replaced by 0, so the access stays in the buffer.  Other builds use i.
@@ -234,6 +245,19 @@ __device__ __forceinline__ void fill_pull_bases(int* sbase, int x, int Lx, int L
     for (int l = threadIdx.x; l < Q; l += blockDim.x)
         sbase[l] = l * plane + wrap_x(x - d_vel[l][0], Lx) * Lz - d_vel[l][1];
 }
+
+// The same bases without a table: away from the periodic seam (3 <= x < Lx - 3, no wrap)
+// sbase[l] = x * Lz + off[l] with off[l] = l * plane - c_lx * Lz - c_lz, one set of offsets
+// for the whole lattice, which the step kernels take from their parameters (no per-block
+// fill, no block barrier).
+inline void pull_offsets(int Lz, int plane, int (&off)[Q]) {
+    for (int l = 0; l < Q; l++) off[l] = l * plane - cx(l) * Lz - cz(l);
+}
+// Push form: pbase[l] = x * Lz + poff[l] off the seam, poff[l] = l * plane + c_lx * Lz + c_lz.
+inline void push_offsets(int Lz, int plane, int (&poff)[Q]) {
+    for (int l = 0; l < Q; l++) poff[l] = l * plane + cx(l) * Lz + cz(l);
+}
+__device__ __forceinline__ bool off_seam(int x, int Lx) { return x >= 3 && x < Lx - 3; }
 
 // Interior tiles, push form: pbase[l] = l * plane + wrap(x + c_lx) * Lz + c_lz, so that
 // population l leaving row z is written at pbase[l] + z.

@@ -245,6 +245,16 @@ __device__ __forceinline__ ffx2 ffx2_two_sum(f32x2 a, f32x2 b) {             // 
     const f32x2 s = x2_add(a, b), bb = x2_sub(s, a);
     return ffx2{s, x2_add(x2_sub(a, x2_sub(s, bb)), x2_sub(b, bb))};
 }
+__device__ __forceinline__ ffx2 ffx2_add_u(const ffx2& a, const ffx2& b) {       // ff_add_u
+    const ffx2 s = ffx2_two_sum(a.hi, b.hi);
+    return ffx2{s.hi, x2_add(s.lo, x2_add(a.lo, b.lo))};
+}
+__device__ __forceinline__ ffx2 ffx2_add(const ffx2& a, const ffx2& b) {         // ff_add
+    const ffx2 s = ffx2_two_sum(a.hi, b.hi);
+    const f32x2 t = x2_add(s.lo, x2_add(a.lo, b.lo));
+    const f32x2 h = x2_add(s.hi, t);
+    return ffx2{h, x2_sub(t, x2_sub(h, s.hi))};
+}
 __device__ __forceinline__ ffx2 ffx2_renorm(const ffx2& a) {                  // ff_renorm
     const f32x2 s = x2_add(a.hi, a.lo);
     return ffx2{s, x2_sub(a.lo, x2_sub(s, a.hi))};
@@ -268,6 +278,17 @@ __device__ __forceinline__ ffx2 ffx2_mul_u(const ffx2& a, const ffx2& b) {      
 __device__ __forceinline__ ffx2 ffx2_mul_f_u(const ffx2& a, f32x2 b) {           // ff_mul_f_u
     const f32x2 p = x2_mul(a.hi, b);
     return ffx2{p, x2_fma(a.lo, b, x2_prod_err(a.hi, b, p))};
+}
+// ff_mul_c3 with the constant c0 in lane 0 and c1 in lane 1
+__device__ __forceinline__ ffx2 ffx2_mul_c3(const ffx2& a, const ff3& c0, const ff3& c1) {
+    const f32x2 chi = x2_pack(c0.hi, c1.hi);
+    const f32x2 p = x2_mul(a.hi, chi);
+    f32x2 e = x2_prod_err(a.hi, chi, p);
+    e = x2_fma(a.hi, x2_pack(c0.lo2, c1.lo2), e);
+    e = x2_fma(a.hi, x2_pack(c0.lo, c1.lo), e);
+    e = x2_fma(a.lo, chi, e);
+    const f32x2 s = x2_add(p, e);
+    return ffx2{s, x2_sub(e, x2_sub(s, p))};
 }
 __device__ __forceinline__ ffx2 ffx2_add_big_u_x4(const ffx2& a, const ffx2& b) {   // ff_add_big_u_x4
     const f32x2 four = x2_pack(4.0f, 4.0f);

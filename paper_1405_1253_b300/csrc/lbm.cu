@@ -164,6 +164,21 @@ static int upload_lattice(int dev) {
     for (int l = 0; l < Q; l++) { vel[l][0] = cx(l); vel[l][1] = cz(l); }
     CU(cudaMemcpyToSymbol(d_shell_first, sfirst, sizeof sfirst));
     CU(cudaMemcpyToSymbol(d_shell_npair, snp, sizeof snp));
+    {   // shell groups (common.cuh): |c|^2 = (1, 2), (4, 8), (5, 10), then 9 across both lanes
+        const int gs[NGROUP][2] = {{1, 2}, {3, 5}, {4, 7}, {6, 6}};
+        ShellGroup g[NGROUP];
+        for (int i = 0; i < NGROUP; i++) {
+            const int a = gs[i][0], b = gs[i][1];
+            if (a != b) {
+                if (snp[a] != snp[b]) return fail(LBM_ECUDA, "shell group %d: unequal pair counts", i);
+                g[i] = ShellGroup{sfirst[a], sfirst[b], snp[a], a, b, (float)shell_c2(a), (float)shell_c2(b)};
+            } else {
+                if (snp[a] != 2) return fail(LBM_ECUDA, "shell group %d: the lone shell needs two pairs", i);
+                g[i] = ShellGroup{sfirst[a], sfirst[a] + 1, 1, a, a, (float)shell_c2(a), (float)shell_c2(a)};
+            }
+        }
+        CU(cudaMemcpyToSymbol(d_groups, g, sizeof g));
+    }
     CU(cudaMemcpyToSymbol(d_vel, vel, sizeof vel));
     CU(cudaDeviceSynchronize());
     g_dev_uploaded[dev] = true;

@@ -115,13 +115,13 @@ __device__ __forceinline__ void thermal_gather(const ThermalSrc<T, LoadNC>& src,
 // One step with thermal walls (tiling t = make_tiling: wall tiles first).  7 blocks per SM:
 // at 8 the wall code spills 84 bytes and the step is no faster.
 __global__ void __launch_bounds__(BLOCK_Z, 7)
-k_step_ff_thermal(const double* __restrict__ fin, double* __restrict__ fout, StepParamsFF p, Tiling t,
-                  ThermalWall w) {
+k_step_ff_thermal(const double* __restrict__ fin, double* __restrict__ fout, const __grid_constant__ StepParamsFF p,
+                  Tiling t, ThermalWall w) {
     __shared__ int sbase[Q];
     __shared__ double s_out[2][WALL_COLS];
     pdl_allow_next();                   // launched with launch_pdl, as k_step_ff
     if (!tile_is_wall(t, blockIdx.x)) {
-        tile_ff<LoadNC, NoMoments, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase);
+        tile_ff<LoadNC, NoMoments, true, true>(fin, fout, p, Shape{p.Lx, p.Lz, p.plane}, t, blockIdx.x, sbase);
         return;
     }
     pdl_wait();
