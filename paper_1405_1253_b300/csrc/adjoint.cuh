@@ -10,8 +10,11 @@
 // pull source of each population: every (l, x, z) is the source of exactly one
 // destination, so the writes never collide.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "init_diag.cuh"
+#include "moments_fix.cuh"
 
 namespace lbm {
 
@@ -77,19 +80,37 @@ __device__ __forceinline__ void adjoint_native_site(const T* __restrict__ ft, co
     [[maybe_unused]] const int n = Q * p.plane;      // element count for bounds-checked builds
     static_for<Q>([&](auto l) { g[l.value] = ft[LBM_IDX(pull_index<decltype(l)::value>(x, z, col, p.Lz, p.plane), n)]; });
     const T r = C::r(), r2 = C::r2();
-    T R = g[0], Jx = T(0), Jz = T(0), E = T(0);
-    static_for<NPAIR>([&](auto k) {
-        constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
-        const T ps = g[A_] + g[B_], ms = g[A_] - g[B_];
-        R += ps;
-        if constexpr (cx(A_) != 0) Jx = fma(T(cx(A_)), ms, Jx);
-        if constexpr (cz(A_) != 0) Jz = fma(T(cz(A_)), ms, Jz);
-        E = fma(T(c2(A_)), ps, E);
-    });
-    const T inv = T(1) / R;
-    const T ux = r * Jx * inv, uz = r * Jz * inv;
-    const T uu = ux * ux + uz * uz;
-    const T T_ = T(0.5) * (r2 * E * inv - uu);
+    T R, inv, ux, uz, uu, T_;
+    if constexpr (std::is_same<T, double>::value) {
+        // FP64: the moments summed exactly in 64-bit fixed point with integer instructions
+        // (moments_fix.cuh), off the FP64 pipe that binds this kernel; rho in units of 2^-60
+        // is scaled back (the ratios do not see the scale)
+        const MomentsFix m = moments_fix(SrcArray{g});
+        const double Rs = __ll2double_rn(m.R);
+        const double invs = 1.0 / Rs;
+        ux = r * __ll2double_rn(m.Jx) * invs;
+        uz = r * __ll2double_rn(m.Jz) * invs;
+        uu = ux * ux + uz * uz;
+        T_ = 1.0 + (fma(d_lat.r2_half, __ll2double_rn(m.E), -Rs) * invs - 0.5 * uu);
+        R = 0x1p-60 * Rs;
+        inv = 0x1p60 * invs;
+    } else {
+        T Rs = g[0], Jx = T(0), Jz = T(0), E = T(0);
+        static_for<NPAIR>([&](auto k) {
+            constexpr int A_ = pair_first(decltype(k)::value), B_ = opp(A_);
+            const T ps = g[A_] + g[B_], ms = g[A_] - g[B_];
+            Rs += ps;
+            if constexpr (cx(A_) != 0) Jx = fma(T(cx(A_)), ms, Jx);
+            if constexpr (cz(A_) != 0) Jz = fma(T(cz(A_)), ms, Jz);
+            E = fma(T(c2(A_)), ps, E);
+        });
+        R = Rs;
+        inv = T(1) / R;
+        ux = r * Jx * inv;
+        uz = r * Jz * inv;
+        uu = ux * ux + uz * uz;
+        T_ = T(0.5) * (r2 * E * inv - uu);
+    }
     const T usx = ux, usz = uz + T(p.us_z), th = T_ + T(p.T_shift) - T(1);
     const T u2 = usx * usx + usz * usz;
     const T a = r * usx, b = r * usz;          // s_l = c_x a + c_z b

@@ -194,7 +194,7 @@ struct AdjSums {
 template <class FSRC>
 struct MomGather {
     const FSRC& src;
-    __device__ __forceinline__ MomentsFix get() const { return moments_ff(src); }
+    __device__ __forceinline__ MomentsFix get() const { return moments_fix(src); }
 };
 struct MomStored {
     const int64_t* __restrict__ m;

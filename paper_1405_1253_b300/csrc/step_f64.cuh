@@ -13,39 +13,27 @@
 // the even part and flip the odd part.
 #pragma once
 #include "common.cuh"
+#include "moments_fix.cuh"
 
 namespace lbm {
 
 // Per-site collide in FP64: g = post-propagate populations, fo = post-collide.
 __device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q], const StepParams& p) {
     const double r = d_lat.r;
-    // moments with integer velocities: rho, J = sum c g, E = sum |c|^2 g
-    double pp[NPAIR], mm[NPAIR];
-    static_for<NPAIR>([&](auto k) {
-        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        pp[k.value] = g[A] + g[B];
-        mm[k.value] = g[A] - g[B];
-    });
-    double rho = g[0], Jx = 0.0, Jz = 0.0;
-    double S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
-    static_for<NPAIR>([&](auto k) {
-        constexpr int A = pair_first(decltype(k)::value);
-        rho += pp[k.value];
-        if constexpr (cx(A) != 0) Jx = fma((double)cx(A), mm[k.value], Jx);
-        if constexpr (cz(A) != 0) Jz = fma((double)cz(A), mm[k.value], Jz);
-        S[shell_of(A)] += pp[k.value];
-    });
-    double E = 0.0;
-    static_for<NSHELL>([&](auto s) {
-        if constexpr (decltype(s)::value > 0) E = fma((double)shell_c2(decltype(s)::value), S[s.value], E);
-    });
-    const double inv = 1.0 / rho;
+    // rho, J = sum c g, E = sum |c|^2 g summed exactly in 64-bit fixed point (unit 2^-60,
+    // moments_fix.cuh) with integer instructions: B300's FP64 pipe, which binds this kernel,
+    // is left the per-site scalars and the equilibrium (about a quarter of its instructions
+    // were these sums).  The scale 2^60 cancels in the ratios and is folded into omega rho.
+    const MomentsFix m = moments_fix(SrcArray{g});
+    const double R = __ll2double_rn(m.R);
+    const double inv = 1.0 / R;
     const double rinv = r * inv;
-    const double ux = Jx * rinv, uz = Jz * rinv;
-    const double T = 0.5 * (d_lat.r2 * E * inv - (ux * ux + uz * uz));
+    const double ux = __ll2double_rn(m.Jx) * rinv, uz = __ll2double_rn(m.Jz) * rinv;
+    // T - 1 = (r^2 E / 2 - rho) / rho - |u|^2 / 2: the O(1) difference in one FMA on the sums
+    const double tm1 = fma(d_lat.r2_half, __ll2double_rn(m.E), -R) * inv - 0.5 * (ux * ux + uz * uz);
     // force shift (Sec. III.A): u_s = u + tau g, T_s = T + tau (1 - tau) g^2 / D
     const double usz = uz + p.us_z;
-    const double th = T + p.T_shift - 1.0;
+    const double th = tm1 + p.T_shift;
     const double u2 = ux * ux + usz * usz;
     // K0, K1, K2 as polynomials in the integer |c|^2 (|xi|^2 = r^2 |c|^2)
     const double r2 = d_lat.r2;
@@ -55,7 +43,7 @@ __device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q
     const double k10 = 1.0 - 0.5 * u2 - 2.0 * th, k11 = r2 * 0.5 * th;
     const double k20 = 0.5 - 0.25 * u2 - 1.5 * th, k21 = r2 * 0.25 * th;
     const double a = r * ux, b = r * usz;          // s_l = c_x a + c_z b
-    const double orho = p.omega * rho;
+    const double orho = p.omega * 0x1p-60 * R;
     fo[0] = fma(p.one_m_omega, g[0], orho * d_lat.w[0] * k00);    // rest population
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);

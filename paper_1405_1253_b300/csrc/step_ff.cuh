@@ -20,6 +20,7 @@
 #pragma once
 #include "common.cuh"
 #include "ff.cuh"
+#include "moments_fix.cuh"
 
 namespace lbm {
 
@@ -125,46 +126,6 @@ struct DstPush {
     }
 };
 
-// Moments of one site in 64-bit fixed point (unit 2^-60): rho, J = sum c g, E = sum |c|^2 g.
-struct MomentsFix {
-    int64_t R, Jx, Jz, E;
-};
-
-// Pass 1: the moments of the site's 37 populations g (src.first<L>()).
-template <class SRC>
-__device__ __forceinline__ MomentsFix moments_ff(const SRC& src) {
-    // pair sums by shell, pair differences grouped by |c_x| and |c_z| (no multiplies)
-    int64_t R, Jx, Jz, E = 0;
-    int64_t S[NSHELL] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int64_t GX[4] = {0, 0, 0, 0}, GZ[4] = {0, 0, 0, 0};
-    {
-        const double v0 = src.template first<0>();
-        R = bits_to_fix60((uint32_t)__double2hiint(v0), (uint32_t)__double2loint(v0));
-    }
-    static_for<NPAIR>([&](auto k) {
-        constexpr int A = pair_first(decltype(k)::value), B = opp(A);
-        const double va = src.template first<A>();
-        const double vb = src.template first<B>();
-        const int64_t fa = bits_to_fix60((uint32_t)__double2hiint(va), (uint32_t)__double2loint(va));
-        const int64_t fb = bits_to_fix60((uint32_t)__double2hiint(vb), (uint32_t)__double2loint(vb));
-        S[shell_of(A)] += fa + fb;
-        constexpr int AX = cx(A) < 0 ? -cx(A) : cx(A), AZ = cz(A) < 0 ? -cz(A) : cz(A);
-        if constexpr (cx(A) > 0) GX[AX] += fa - fb;
-        if constexpr (cx(A) < 0) GX[AX] += fb - fa;
-        if constexpr (cz(A) > 0) GZ[AZ] += fa - fb;
-        if constexpr (cz(A) < 0) GZ[AZ] += fb - fa;
-    });
-    static_for<NSHELL>([&](auto s) {
-        constexpr int SS = decltype(s)::value;
-        if constexpr (SS > 0) {
-            R += S[SS];
-            E += (int64_t)shell_c2(SS) * S[SS];
-        }
-    });
-    Jx = GX[1] + 2 * GX[2] + 3 * GX[3];
-    Jz = GZ[1] + 2 * GZ[2] + 3 * GZ[3];
-    return MomentsFix{R, Jx, Jz, E};
-}
 
 // The rest of the collide of one site from its moments m: per-site scalars, equilibrium,
 // relaxation; src.again / src.pair give the populations g again, dst takes the results.
@@ -285,7 +246,7 @@ struct MomentsOut {
 template <class SRC, class DST, class MOUT = NoMoments>
 __device__ __forceinline__ void site_ff(const SRC& src, const DST& dst, const StepParamsFF& p,
                                         const MOUT& mo = MOUT{}, int o = 0) {
-    const MomentsFix m = moments_ff(src);
+    const MomentsFix m = moments_fix(src);
     mo.put(m, o);
     collide_ff(m, src, dst, p);
 }
