@@ -142,21 +142,22 @@ struct LamOwn {
     __device__ __forceinline__ uint32_t hiword() const {
         uint32_t v;
         const double* p = lam + LBM_IDX(L * plane + o, Q * plane);
-        asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"((const char*)p + 4));
+        asm("ld.global.nc.L2::cache_hint.L2::256B.u32 %0, [%1], %2;" : "=r"(v) : "l"((const char*)p + 4),
+            "l"(LoadNC::pol_keep()));     // lam is read twice more (the sums, the output)
         return v;
     }
     // re-reads; LAST: the output pass, the final use of each value (evict-first in L1)
     template <int L, bool LAST = false>
     __device__ __forceinline__ double again() const {
         const double* q = lam + LBM_IDX(L * plane + o, Q * plane);
-        return LAST ? LoadNC::ld_last(q) : LoadNC::ld_again(q);
+        return LAST ? LoadNC::ld_last(q) : LoadNC::ld_again_keep(q);
     }
     template <bool LAST = false>
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
         const double* qa = lam + LBM_IDX(pi.A * plane + o, Q * plane);
         const double* qb = lam + LBM_IDX(pi.B * plane + o, Q * plane);
-        va = LAST ? LoadNC::ld_last(qa) : LoadNC::ld_again(qa);
-        vb = LAST ? LoadNC::ld_last(qb) : LoadNC::ld_again(qb);
+        va = LAST ? LoadNC::ld_last(qa) : LoadNC::ld_again_keep(qa);
+        vb = LAST ? LoadNC::ld_last(qb) : LoadNC::ld_again_keep(qb);
     }
 };
 
@@ -170,16 +171,16 @@ struct DstSource {
     int zoff;             // the row z, or the site x Lz + z with the offsets
     template <int L>
     __device__ __forceinline__ void put(double v) const {
-        if constexpr (WALL) out[LBM_IDX((ad.template src<L, true>()), Q * ad.plane)] = v;
-        else out[LBM_IDX(sbase[L] + zoff, Q * ad.plane)] = v;
+        if constexpr (WALL) st_stream(out + LBM_IDX((ad.template src<L, true>()), Q * ad.plane), v);
+        else st_stream(out + LBM_IDX(sbase[L] + zoff, Q * ad.plane), v);
     }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
         if constexpr (WALL) {
-            out[LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane)] = va;
-            out[LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane)] = vb;
+            st_stream(out + LBM_IDX((ad.template src_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane), va);
+            st_stream(out + LBM_IDX((ad.template src_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane), vb);
         } else {
-            out[LBM_IDX(sbase[pi.A] + zoff, Q * ad.plane)] = va;
-            out[LBM_IDX(sbase[pi.B] + zoff, Q * ad.plane)] = vb;
+            st_stream(out + LBM_IDX(sbase[pi.A] + zoff, Q * ad.plane), va);
+            st_stream(out + LBM_IDX(sbase[pi.B] + zoff, Q * ad.plane), vb);
         }
     }
 };
@@ -393,8 +394,8 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
         if (mom) {
             adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
         } else {
-            const SrcGlobal<true, LoadNC> src{ft, ad, sbase, 0};
-            adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC>>{src}, lsrc, dst, p);
+            const SrcGlobal<true, LoadNC, false, true> src{ft, ad, sbase, 0};
+            adjoint_site_ff(MomGather<SrcGlobal<true, LoadNC, false, true>>{src}, lsrc, dst, p);
         }
         return;
     }
@@ -406,8 +407,8 @@ __device__ __forceinline__ void adjoint_tile_ff(const double* __restrict__ ft, c
         if (mom) {
             adjoint_site_ff(MomStored{mom, p.plane, ad.dst()}, lsrc, dst, p);
         } else {
-            const SrcGlobal<false, LoadNC> src{ft, ad, bases, zoff};
-            adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC>>{src}, lsrc, dst, p);
+            const SrcGlobal<false, LoadNC, false, true> src{ft, ad, bases, zoff};
+            adjoint_site_ff(MomGather<SrcGlobal<false, LoadNC, false, true>>{src}, lsrc, dst, p);
         }
     };
     const int x = tile_column(t, b);

@@ -42,10 +42,12 @@ __device__ __forceinline__ ff dsplit(double x) {
 __device__ __forceinline__ ff i64_to_ff(int64_t v) { return dsplit(__ll2double_rn(v)); }
 
 // Pull sources of one site, read from global memory (interior sites through the pull bases
-// of the tile, wall sites through the bounce-back rule).  KEEP: the first reads of the shells
-// |c|^2 <= 5, which the step's second pass reads first, are kept in L1 in preference
-// (shells 1-4: +0.7%; all shells: +0.4%; the others marked evict-first: -3.5%).
-template <bool WALL, class LD, bool KEEP = false>
+// of the tile, wall sites through the bounce-back rule).  KEEP (the step, which reads every
+// value twice): the first reads are kept in L2 for the second pass, and those of the shells
+// |c|^2 <= 5, which the second pass reads first, in L1 too (shells 1-4: +0.7%; all shells:
+// +0.4%; the others marked evict-first: -3.5%).  ONCE (the adjoint's gather, the only read):
+// evict-first.
+template <bool WALL, class LD, bool KEEP = false, bool ONCE = false>
 struct SrcGlobal {
     const double* __restrict__ fin;
     const SiteAddr& ad;
@@ -59,6 +61,8 @@ struct SrcGlobal {
     template <int L>
     __device__ __forceinline__ double first() const {
         if constexpr (KEEP && shell_of(L) >= 1 && shell_of(L) <= 4) return LD::ld_keep(fin + idx<L>());
+        else if constexpr (KEEP) return LD::ld_first(fin + idx<L>());
+        else if constexpr (ONCE) return LD::ld_once(fin + idx<L>());
         else return LD::ld(fin + idx<L>());
     }
     // second reads (the step's last use of each value)
@@ -95,10 +99,10 @@ struct DstSite {
     double* __restrict__ fout;
     int o, plane;
     template <int L>
-    __device__ __forceinline__ void put(double v) const { fout[LBM_IDX(L * plane + o, Q * plane)] = v; }
+    __device__ __forceinline__ void put(double v) const { st_stream(fout + LBM_IDX(L * plane + o, Q * plane), v); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
-        fout[LBM_IDX(pi.A * plane + o, Q * plane)] = va;
-        fout[LBM_IDX(pi.B * plane + o, Q * plane)] = vb;
+        st_stream(fout + LBM_IDX(pi.A * plane + o, Q * plane), va);
+        st_stream(fout + LBM_IDX(pi.B * plane + o, Q * plane), vb);
     }
 };
 
