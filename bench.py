@@ -50,11 +50,11 @@ def measured_peaks():
 
 # The sources that define each step kernel (its counters stay valid while these are unchanged).
 KERNEL_SOURCES = {
-    "k_step_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh"),
-    "k_step_f64": ("lattice.cuh", "common.cuh", "step_f64.cuh"),
+    "k_step_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh"),
+    "k_step_f64": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_f64.cuh"),
     "k_step_f32": ("lattice.cuh", "common.cuh", "step_f32.cuh"),
-    "k_adjoint_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
-    "k_adjoint_ff_moments": ("lattice.cuh", "common.cuh", "ff.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
+    "k_adjoint_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
+    "k_adjoint_ff_moments": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
 }
 
 
@@ -355,15 +355,17 @@ def bench_ensemble(torch, lbm, prec, steps, stream, tune_steps=20):
 def bench_adjoint(torch):
     """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and backward
     (recompute + adjoint) wall times and device memory, for the three backward stores of the
-    float-float driver (recomputed moment records, moment records taped in the forward,
-    segment states) and for an FP32-storage run."""
+    float-float driver (recomputed moment records, with the recompute of the next segment
+    overlapping the adjoint of the current one on a second stream and without; moment records
+    taped in the forward; segment states) and for an FP32-storage run."""
     from paper_1405_1253_b300 import adjoint
     lat = W.GRADIENT_256x512
     out = {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (f64_ff)"}
     m = lat.modes()
-    for store, prec in (("moments", "f64_ff"), ("tape", "f64_ff"), ("states", "f64_ff"), ("states", "f32")):
-        key = store if prec == "f64_ff" else "f32"
-        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store)
+    for key, store, prec, pipe in (("moments", "moments", "f64_ff", True), ("moments_serial", "moments", "f64_ff", False),
+                                   ("tape", "tape", "f64_ff", False), ("states", "states", "f64_ff", False),
+                                   ("f32", "states", "f32", False)):
+        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store, pipeline=pipe)
         drv.forward(m.amp_lo, m.amp_hi)      # warm
         drv.backward()
         drv.forward(m.amp_lo, m.amp_hi)

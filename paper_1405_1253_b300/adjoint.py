@@ -11,9 +11,11 @@ adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA l
 this module only orders the calls and owns the buffers (through PyTorch).
 
 Memory: (N/K) checkpoints and 2 adjoint fields, each 37 Lx Lz doubles, and per segment either
-(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through.  The
-"tape" store instead records the moments of all N steps during the forward pass (32 bytes per
-site and step, no checkpoints), so the backward recomputes nothing.
+(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through (two sets
+of records when the recompute of the next segment overlaps the adjoint of the current one on a
+second stream, the default).  The "tape" store instead records the moments of all N steps
+during the forward pass (32 bytes per site and step, no checkpoints), so the backward
+recomputes nothing.
 """
 from __future__ import annotations
 
@@ -50,10 +52,12 @@ class WidthGradient:
     forward records the moments of every step (N x 32 bytes per site; ckpt only sets the
     length of each adjoint chain call) and the backward runs the adjoint steps alone.
     walls=(T_bottom, T_top): thermal walls (lbm_set_walls) in the forward and the adjoint
-    (f64_ff, states)."""
+    (f64_ff, states).  pipeline (store "moments"): the recompute of segment s - 1 runs on a
+    second stream while the adjoint chain of segment s runs (two sets of records); the
+    gradient is the same bit for bit."""
 
     def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None,
-                 walls=None):
+                 walls=None, pipeline: bool = True):
         import torch
         if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
             raise ValueError("nsteps must be a positive multiple of ckpt")
@@ -68,6 +72,7 @@ class WidthGradient:
         if self.store not in ("moments", "states", "tape") or (
                 self.store != "states" and (prec != "f64_ff" or walls)):
             raise ValueError("store is 'states', or 'moments' / 'tape' with prec 'f64_ff' and bounce-back walls")
+        self.pipeline = False
         self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
         if walls is not None:                      # thermal walls at (T_bottom, T_top)
             self.L.set_walls(True, *walls)
@@ -86,10 +91,20 @@ class WidthGradient:
             self.seg = torch.empty((self.K - 1, n), dtype=dt, device=dev)
             seg_bytes = self.seg.element_size() * n * (self.K - 1)
         else:
-            # moments of the K steps of a segment, and two states to step through
-            self.moms = torch.empty((self.K, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
+            # moments of the K steps of a segment, and two states to step through; with the
+            # pipeline, two sets of records: the recompute of segment s - 1 (a second context on
+            # a second stream) fills one while the adjoint chain of segment s reads the other
+            self.pipeline = bool(pipeline) and self.N // self.K > 1
+            nset = 2 if self.pipeline else 1
+            self.moms_sets = [torch.empty((self.K, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
+                              for _ in range(nset)]
+            self.moms = self.moms_sets[0]
             self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
-            seg_bytes = self.moms.numel() * 8 + 2 * 8 * n
+            seg_bytes = nset * self.moms.numel() * 8 + 2 * 8 * n
+            if self.pipeline:
+                self.rec_stream = torch.cuda.Stream(device=dev)
+                self.Lrec = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=self.rec_stream)
+                seg_bytes += 2 * 8 * n          # the recompute context's own two buffers
         self.lam = [torch.empty(n, dtype=dt, device=dev) for _ in range(2)]
         es = self.lam[0].element_size()
         self.stats = AdjointStats(checkpoint_bytes=es * n * len(self.ckpts), segment_bytes=seg_bytes,
@@ -141,7 +156,11 @@ class WidthGradient:
         t0 = time.perf_counter()
         cur, nxt = self.lam
         self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
-        for s in range(self.N // self.K - 1, -1, -1):
+        segments = range(self.N // self.K - 1, -1, -1)
+        if self.store == "moments" and self.pipeline:
+            cur = self._backward_pipelined(cur, nxt)
+            segments = ()
+        for s in segments:
             if self.store == "tape":
                 # the K recorded steps of segment s, adjoint steps only
                 flip = self.L.adjoint_chain_moments([self.moms[s * self.K + j] for j in range(self.K)], cur, nxt)
@@ -169,8 +188,44 @@ class WidthGradient:
         self.stats.backward_s = time.perf_counter() - t0
         return g_lo, g_hi
 
+    def _backward_pipelined(self, cur, nxt):
+        """The moment-record backward with the recompute of segment s - 1 (recording context,
+        second stream) overlapping the adjoint chain of segment s (the context's stream).  The
+        adjoint of s waits for the records of s; the recompute of s - 1 reuses the record set
+        of s + 1, so it waits for that segment's adjoint.  Returns the tensor holding lam_0."""
+        torch = self.torch
+        S = self.N // self.K
+        main = self.L.stream
+        rec = self.rec_stream
+        ev_rec = [torch.cuda.Event() for _ in range(S)]
+        ev_adj = [torch.cuda.Event() for _ in range(S)]
+        rec.wait_stream(main)                     # the checkpoints and lam_N are written on main
+
+        def record(s):
+            moms = self.moms_sets[s % 2]
+            if s + 2 < S:
+                rec.wait_event(ev_adj[s + 2])     # its record set was read by the adjoint of s + 2
+            self.Lrec.record_moments(self.ckpts[s], self.work[0], self.work[1], [moms[j] for j in range(self.K)])
+            ev_rec[s].record(rec)
+            self.stats.recompute_steps += self.K
+
+        record(S - 1)
+        for s in range(S - 1, -1, -1):
+            main.wait_event(ev_rec[s])
+            moms = self.moms_sets[s % 2]
+            flip = self.L.adjoint_chain_moments([moms[j] for j in range(self.K)], cur, nxt)
+            ev_adj[s].record(main)
+            if flip == 1:
+                cur, nxt = nxt, cur
+            self.stats.adjoint_steps += self.K
+            if s > 0:
+                record(s - 1)
+        return cur
+
     def close(self):
         self.L.close()
+        if getattr(self, "Lrec", None) is not None:
+            self.Lrec.close()
 
 
 def _make_function():

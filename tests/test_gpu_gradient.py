@@ -87,13 +87,15 @@ def test_gradient_vs_finite_differences_256x512_2000_steps(adj):
 
 def test_moment_store_gives_the_same_gradient(adj):
     """The three backward stores of the float-float driver (segment states, recomputed moment
-    records, moment records taped in the forward) give the same loss and the same amplitude
-    and phase gradients bit for bit; the tape recomputes no step."""
+    records with and without the recompute overlapped on a second stream, moment records taped
+    in the forward) give the same loss and the same amplitude and phase gradients bit for bit;
+    the tape recomputes no step."""
     lat = W.Lattice(40, 96, tau=0.8, grav=1e-4, K=3, sigma=1.0, seed=25)
     m = lat.modes()
     out = []
-    for store in ("states", "moments", "tape"):
-        drv = adj.WidthGradient(lat, 60, 20, store=store)
+    for store, pipe in (("states", False), ("moments", False), ("moments", True), ("tape", False)):
+        drv = adj.WidthGradient(lat, 60, 20, store=store, pipeline=pipe)
+        assert drv.pipeline == pipe
         val = drv.forward(m.amp_lo, m.amp_hi)
         g = np.concatenate(drv.backward())
         out.append((val, g, np.concatenate(drv.grad_phases)))
