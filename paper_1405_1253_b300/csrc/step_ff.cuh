@@ -79,13 +79,15 @@ struct SrcGlobal {
     }
 };
 
-// The site's own populations (push form: collide first, then move).
+// The site's own populations (push form: collide first, then move); the first reads are kept
+// in L2 for the second pass and the results stored streaming, as in the pull form (push step
+// 0.2769 -> 0.2667 ms on 1024 x 2048).
 template <class LD>
 struct SrcOwn {
     const double* __restrict__ fin;
     int o, plane;
     template <int L>
-    __device__ __forceinline__ double first() const { return LD::ld(fin + LBM_IDX(L * plane + o, Q * plane)); }
+    __device__ __forceinline__ double first() const { return LD::ld_first(fin + LBM_IDX(L * plane + o, Q * plane)); }
     template <int L>
     __device__ __forceinline__ double again() const { return LD::ld_last(fin + LBM_IDX(L * plane + o, Q * plane)); }
     __device__ __forceinline__ void pair(const PairInfo& pi, double& va, double& vb) const {
@@ -116,16 +118,16 @@ struct DstPush {
     int zoff;             // the row z, or the site x Lz + z with the offsets
     template <int L>
     __device__ __forceinline__ void put(double v) const {
-        if constexpr (WALL) fout[LBM_IDX((ad.template push_dst<L, true>()), Q * ad.plane)] = v;
-        else fout[LBM_IDX(pbase[L] + zoff, Q * ad.plane)] = v;
+        if constexpr (WALL) st_stream(fout + LBM_IDX((ad.template push_dst<L, true>()), Q * ad.plane), v);
+        else st_stream(fout + LBM_IDX(pbase[L] + zoff, Q * ad.plane), v);
     }
     __device__ __forceinline__ void pair(const PairInfo& pi, double va, double vb) const {
         if constexpr (WALL) {
-            fout[LBM_IDX((ad.template push_dst_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane)] = va;
-            fout[LBM_IDX((ad.template push_dst_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane)] = vb;
+            st_stream(fout + LBM_IDX((ad.template push_dst_rt<true>(pi.A, pi.B, pi.cx, pi.cz)), Q * ad.plane), va);
+            st_stream(fout + LBM_IDX((ad.template push_dst_rt<true>(pi.B, pi.A, -pi.cx, -pi.cz)), Q * ad.plane), vb);
         } else {
-            fout[LBM_IDX(pbase[pi.A] + zoff, Q * ad.plane)] = va;
-            fout[LBM_IDX(pbase[pi.B] + zoff, Q * ad.plane)] = vb;
+            st_stream(fout + LBM_IDX(pbase[pi.A] + zoff, Q * ad.plane), va);
+            st_stream(fout + LBM_IDX(pbase[pi.B] + zoff, Q * ad.plane), vb);
         }
     }
 };
