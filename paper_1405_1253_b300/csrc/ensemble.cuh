@@ -78,11 +78,14 @@ __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, 
 // per-step kernel takes the register budgets of the single-lattice kernels: 32 warps per SM
 // for the float-float tile (64 registers, as k_step_ff) and 24 for the FP32 tile (80, as
 // k_step_f32).  The persistent kernel, which carries its queue and barrier state through
-// every tile, keeps 20 warps (96 registers; at 64 it spills 168 bytes).
+// every tile, is held to 32 warps for the float-float tile (64 registers, spilling ~220 bytes)
+// and 28 for the FP32 tile (72 registers): more resident warps outweigh the spills (measured
+// on the 48-lattice set: 6,468 -> 6,957 and 13,030 -> 15,179 MLUPS against 20 warps at 96
+// registers).
 template <class P, int TZ>
 constexpr int ens_step_min_blocks() { return (std::is_same<P, StepParamsFF>::value ? 1024 : 768) / TZ; }
-template <int TZ>
-constexpr int ens_persistent_min_blocks() { return TZ == 64 ? 10 : TZ == 128 ? 5 : 2; }
+template <class P, int TZ>
+constexpr int ens_persistent_min_blocks() { return (std::is_same<P, StepParamsFF>::value ? 1024 : 896) / TZ; }
 
 template <class P, int TZ>
 __global__ void __launch_bounds__(TZ, ens_step_min_blocks<P, TZ>())
@@ -120,7 +123,7 @@ __device__ __forceinline__ bool ens_wait(const unsigned int* ctr, unsigned int n
 constexpr int ENS_CACHE = 64;
 
 template <class P, int TZ>
-__global__ void __launch_bounds__(TZ, ens_persistent_min_blocks<TZ>())
+__global__ void __launch_bounds__(TZ, ens_persistent_min_blocks<P, TZ>())
 k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_tiles,
                  EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
     __shared__ int sbase[Q];
