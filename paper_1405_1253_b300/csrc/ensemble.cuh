@@ -7,9 +7,10 @@
 //   k_ens_step:       one launch per time step over all tiles of all lattices (the launch
 //                     boundary separates the steps);
 //   k_ens_persistent: ONE launch for n steps.  Co-resident CTAs (cooperative launch) take
-//                     work items (step, tile) from a step-major queue; before a tile of
-//                     step s of lattice i runs, the CTA waits until all tiles of step s-1 of
-//                     lattice i are done (per-lattice step barrier: a completion counter).
+//                     work items (step, ens_item consecutive tiles of one lattice) from a
+//                     step-major queue; before an item of step s of lattice i runs, the CTA
+//                     waits until all tiles of step s-1 of lattice i are done (per-lattice
+//                     step barrier: a completion counter of tiles).
 //                     The wait is a bounded spin: past the limit it sets the error word and
 //                     the CTA leaves, and every other CTA leaves at its next wait.  Data
 //                     written inside the launch is read through L2 (LoadCG), never a stale L1.
@@ -32,7 +33,15 @@ struct EnsLattice {
     Tiling t;
     int tile_begin;   // first global tile number
     int ntiles;
+    int item_begin;   // first persistent work item of the lattice (ens_item tiles per item)
 };
+
+// Tiles per work item of the persistent kernel: one queue fetch, lattice search, barrier wait
+// and completion count serve that many consecutive tiles of one lattice.  FP32: 8 (the 48-lattice
+// set, 200 steps: 15,172 MLUPS with one tile per item, 16,264 / 17,063 / 17,524 with 2 / 4 / 8);
+// float-float: 1 (6,966 against 6,820-6,887: the tile loop raises the spill of its 64-register
+// budget).
+constexpr int ens_item(bool ff) { return ff ? 1 : 8; }
 
 struct EnsControl {   // device words, reset before every persistent launch
     unsigned int queue;
@@ -46,6 +55,16 @@ __device__ __forceinline__ int ens_find(const EnsLattice* __restrict__ lats, int
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (lats[mid].tile_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+// Lattice owning persistent work item j of a step (binary search over item_begin).
+__device__ __forceinline__ int ens_find_item(const EnsLattice* __restrict__ lats, int n, int j) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (lats[mid].item_begin <= j) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -124,13 +143,13 @@ constexpr int ENS_CACHE = 64;
 
 template <class P, int TZ>
 __global__ void __launch_bounds__(TZ, ens_persistent_min_blocks<P, TZ>())
-k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_tiles,
+k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_items,
                  EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
     __shared__ int sbase[Q];
     __shared__ unsigned int s_item, s_next;
     __shared__ int s_ok;
     __shared__ unsigned int s_seen[ENS_CACHE];
-    const unsigned int total = (unsigned int)nsteps * (unsigned int)total_tiles;
+    const unsigned int total = (unsigned int)nsteps * (unsigned int)total_items;
     for (int i = threadIdx.x; i < ENS_CACHE; i += blockDim.x) s_seen[i] = 0u;
     if (threadIdx.x == 0) s_next = atomicAdd(&ctl->queue, 1u);
     __syncthreads();
@@ -140,9 +159,9 @@ k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, in
             int ok = 1;
             if (it < total) {
                 s_next = atomicAdd(&ctl->queue, 1u);        // next item, fetched ahead
-                const int s = (int)(it / (unsigned int)total_tiles);
-                const int b = (int)(it % (unsigned int)total_tiles);
-                const int i = ens_find(lats, n, b);
+                const int s = (int)(it / (unsigned int)total_items);
+                const int j = (int)(it % (unsigned int)total_items);
+                const int i = ens_find_item(lats, n, j);
                 if (s > 0 || extra_wait) {
                     const unsigned int need = (unsigned int)s * (unsigned int)lats[i].ntiles + extra_wait;
                     if (i >= ENS_CACHE || s_seen[i] < need) {
@@ -157,15 +176,25 @@ k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, in
         __syncthreads();
         const unsigned int it = s_item;
         if (it >= total || !s_ok) break;
-        const int s = (int)(it / (unsigned int)total_tiles);
-        const int b = (int)(it % (unsigned int)total_tiles);
-        const int i = ens_find(lats, n, b);
+        const int s = (int)(it / (unsigned int)total_items);
+        const int j = (int)(it % (unsigned int)total_items);
+        const int i = ens_find_item(lats, n, j);
         const EnsLattice L = lats[i];
-        ens_tile<LoadCG>(L, b - L.tile_begin, s, q, sbase);
-        __syncthreads();   // all stores of the tile issued; s_item / sbase may be reused
+        constexpr int KT = ens_item(std::is_same<P, StepParamsFF>::value);
+        const int t0 = (j - L.item_begin) * KT;
+        const int t1 = min(t0 + KT, L.ntiles);
+        if constexpr (KT == 1) {
+            ens_tile<LoadCG>(L, t0, s, q, sbase);
+            __syncthreads();   // all stores of the tile issued; s_item / sbase may be reused
+        } else {
+            for (int tl = t0; tl < t1; tl++) {
+                ens_tile<LoadCG>(L, tl, s, q, sbase);
+                __syncthreads();   // all stores of the tile issued; sbase may be refilled
+            }
+        }
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(&done[i], 1u);
+            atomicAdd(&done[i], (unsigned int)(t1 - t0));
         }
     }
 }

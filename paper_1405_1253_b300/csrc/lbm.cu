@@ -1038,6 +1038,7 @@ struct lbm_ensemble {
     std::vector<EnsLattice> h_lats;
     EnsLattice* d_lats = nullptr;
     int total_tiles = 0;
+    int total_items = 0;     // persistent work items per step
     EnsControl* d_ctl = nullptr;
     unsigned int* d_done = nullptr;
     int mode = 1;            // 0: one launch per step, 1: one persistent launch
@@ -1052,7 +1053,7 @@ struct lbm_ensemble {
 
 static int ens_layout(lbm_ensemble* e) {
     e->h_lats.resize(e->n);
-    int tb = 0;
+    int tb = 0, ib = 0;
     for (int i = 0; i < e->n; i++) {
         lbm_ctx* c = e->ctx[i];
         NEED_BOUNCE_BACK(c, "an ensemble");
@@ -1064,9 +1065,13 @@ static int ens_layout(lbm_ensemble* e) {
         L.t = make_tiling(c->Lx, c->Lz, e->tz);
         L.tile_begin = tb;
         L.ntiles = tiling_blocks(L.t);
+        L.item_begin = ib;
         tb += L.ntiles;
+        const int kt = ens_item(e->prec == LBM_F64_FF);
+        ib += (L.ntiles + kt - 1) / kt;
     }
     e->total_tiles = tb;
+    e->total_items = ib;
     // stream-ordered: kernels of an earlier call on the same stream still read the old table
     // (a pageable source is staged before the call returns, so h_lats may change afterwards)
     CU(cudaMemcpyAsync(e->d_lats, e->h_lats.data(), e->n * sizeof(EnsLattice), cudaMemcpyHostToDevice,
@@ -1083,7 +1088,7 @@ static int ens_launch_tz(lbm_ensemble* e, const P& q, int nsteps) {
         }
         return LBM_OK;
     }
-    if ((long long)nsteps * e->total_tiles >= (1LL << 32)) return fail(LBM_EINVAL, "too many work items for one launch");
+    if ((long long)nsteps * e->total_items >= (1LL << 32)) return fail(LBM_EINVAL, "too many work items for one launch");
     int per_sm = 0, nsm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_persistent<P, TZ>, TZ, 0));
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->device));
@@ -1102,7 +1107,7 @@ static int ens_launch_tz(lbm_ensemble* e, const P& q, int nsteps) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     CU(cudaLaunchKernelEx(&cfg, k_ens_persistent<P, TZ>, (const EnsLattice*)e->d_lats, e->n, q, nsteps,
-                          e->total_tiles, e->d_ctl, e->d_done, e->spin_limit, e->extra_wait));
+                          e->total_items, e->d_ctl, e->d_done, e->spin_limit, e->extra_wait));
     return LBM_OK;
 }
 
