@@ -37,11 +37,12 @@ struct EnsLattice {
 };
 
 // Tiles per work item of the persistent kernel: one queue fetch, lattice search, barrier wait
-// and completion count serve that many consecutive tiles of one lattice.  FP32: 8 (the 48-lattice
-// set, 200 steps: 15,172 MLUPS with one tile per item, 16,264 / 17,063 / 17,524 with 2 / 4 / 8);
-// float-float: 1 (6,966 against 6,820-6,887: the tile loop raises the spill of its 64-register
-// budget).
-constexpr int ens_item(bool ff) { return ff ? 1 : 8; }
+// and completion count serve that many consecutive tiles of one lattice (the 48-lattice set,
+// 200 steps, FP32: 15,172 MLUPS with one tile per item, 16,264 / 17,063 / 17,524 with 2 / 4 / 8;
+// float-float at 28 warps per SM: 6,841 with one, 7,064 / 7,116 / 7,110 with 4 / 8 / 16).
+// Letting consecutive tiles of one column share the pull-base table (no refill, no barrier
+// between them) was slower: 6,657 and 17,294.
+constexpr int ens_item(bool) { return 8; }
 
 struct EnsControl {   // device words, reset before every persistent launch
     unsigned int queue;
@@ -97,14 +98,15 @@ __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, 
 // per-step kernel takes the register budgets of the single-lattice kernels: 32 warps per SM
 // for the float-float tile (64 registers, as k_step_ff) and 24 for the FP32 tile (80, as
 // k_step_f32).  The persistent kernel, which carries its queue and barrier state through
-// every tile, is held to 32 warps for the float-float tile (64 registers, spilling ~220 bytes)
-// and 28 for the FP32 tile (72 registers): more resident warps outweigh the spills (measured
-// on the 48-lattice set: 6,468 -> 6,957 and 13,030 -> 15,179 MLUPS against 20 warps at 96
-// registers).
+// every tile, is held to 28 warps per SM (72 registers): more resident warps outweigh the
+// spills (measured on the 48-lattice set with one tile per work item: 6,468 -> 6,841 / 6,957
+// float-float at 28 / 32 warps and 13,030 -> 15,179 FP32 at 28, against 20 warps at 96
+// registers; with 8-tile work items 28 warps are best for both: 7,116 against 6,898 float-float
+// at 32 and 7,047 at 24).
 template <class P, int TZ>
 constexpr int ens_step_min_blocks() { return (std::is_same<P, StepParamsFF>::value ? 1024 : 768) / TZ; }
 template <class P, int TZ>
-constexpr int ens_persistent_min_blocks() { return (std::is_same<P, StepParamsFF>::value ? 1024 : 896) / TZ; }
+constexpr int ens_persistent_min_blocks() { return 896 / TZ; }
 
 template <class P, int TZ>
 __global__ void __launch_bounds__(TZ, ens_step_min_blocks<P, TZ>())
@@ -183,14 +185,9 @@ k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, in
         constexpr int KT = ens_item(std::is_same<P, StepParamsFF>::value);
         const int t0 = (j - L.item_begin) * KT;
         const int t1 = min(t0 + KT, L.ntiles);
-        if constexpr (KT == 1) {
-            ens_tile<LoadCG>(L, t0, s, q, sbase);
+        for (int tl = t0; tl < t1; tl++) {
+            ens_tile<LoadCG>(L, tl, s, q, sbase);
             __syncthreads();   // all stores of the tile issued; s_item / sbase may be reused
-        } else {
-            for (int tl = t0; tl < t1; tl++) {
-                ens_tile<LoadCG>(L, tl, s, q, sbase);
-                __syncthreads();   // all stores of the tile issued; sbase may be refilled
-            }
         }
         if (threadIdx.x == 0) {
             __threadfence();
