@@ -40,8 +40,9 @@ struct EnsLattice {
 // and completion count serve that many consecutive tiles of one lattice (the 48-lattice set,
 // 200 steps, FP32: 15,172 MLUPS with one tile per item, 16,264 / 17,063 / 17,524 with 2 / 4 / 8;
 // float-float at 28 warps per SM: 6,841 with one, 7,064 / 7,116 / 7,110 with 4 / 8 / 16).
-// Letting consecutive tiles of one column share the pull-base table (no refill, no barrier
-// between them) was slower: 6,657 and 17,294.
+// Consecutive tiles of one column sharing the pull-base table (no refill, no barrier between
+// them) were slower while every thread also held the lattice record in registers (6,657 and
+// 17,294); with the record in shared memory they are faster (ens_item_tile).
 constexpr int ens_item(bool) { return 8; }
 
 struct EnsControl {   // device words, reset before every persistent launch
@@ -92,6 +93,43 @@ __device__ __forceinline__ void ens_tile(const EnsLattice& L, int local, int s, 
     q.Lz = L.Lz;
     q.plane = L.plane;
     tile_f32<LD>(fin, fout, q, L.t, local);
+}
+
+// The same for the tiles of one work item of the persistent kernel, with the item's pull-base
+// tables in shared memory shared across its tiles: an interior tile fills a table only when
+// its column differs from the previous tile's (consecutive tiles of one column have the same
+// bases), alternating between two tables, so that each fill needs one block barrier and no
+// barrier separates the tiles (the fill barrier also orders every thread's use of the other
+// table, two fills back, before its refill).  col / cur (block-uniform): the column of the
+// current table and its index, -1 / 0 at the start of an item.
+template <class LD>
+__device__ __forceinline__ void ens_item_tile(const EnsLattice& L, int tl, int s, const StepParamsFF& qf,
+                                             int (*tabs)[Q], int& col, int& cur) {
+    const bool odd = (L.cur + s) & 1;
+    const double* fin = (const double*)(odd ? L.buf[1] : L.buf[0]);
+    double* fout = (double*)(odd ? L.buf[0] : L.buf[1]);
+    SiteAddr ad;
+    bool wall;
+    if (tile_is_wall(L.t, tl)) {
+        if (!ad.setup(L.Lx, L.Lz, L.plane, L.t, tl, wall)) return;
+        site_ff(SrcGlobal<true, LD, true>{fin, ad, tabs[0], 0}, DstSite{fout, ad.dst(), L.plane}, qf);
+        return;
+    }
+    const int x = tile_column(L.t, tl);
+    if (x != col) {
+        cur ^= 1;
+        fill_pull_bases(tabs[cur], x, L.Lx, L.Lz, L.plane);
+        __syncthreads();
+        col = x;
+    }
+    if (!ad.setup(L.Lx, L.Lz, L.plane, L.t, tl, wall)) return;
+    site_ff(SrcGlobal<false, LD, true>{fin, ad, tabs[cur], ad.z}, DstSite{fout, ad.dst(), L.plane}, qf);
+}
+// FP32 tiles use no shared table.
+template <class LD>
+__device__ __forceinline__ void ens_item_tile(const EnsLattice& L, int tl, int s, const StepParamsF& qs,
+                                             int (*)[Q], int&, int&) {
+    ens_tile<LD>(L, tl, s, qs, nullptr);
 }
 
 // Resident blocks per SM requested from the compiler for a tile height of TZ threads.  The
@@ -146,14 +184,17 @@ __device__ __forceinline__ bool ens_wait(const unsigned int* ctr, unsigned int n
 // tiles, had raised the spill at 72 registers from 40 to 128 bytes (float-float) and from 56
 // to 140 (FP32); reading it from shared memory took the 48-lattice set from 7,130 to 7,366
 // MLUPS float-float and from 17,522 to 19,060 FP32 (200 steps; per-step launches 7,420 and
-// 18,490, which the same change left unchanged).
+// 18,490, which the same change left unchanged).  The tiles of an item share their pull-base
+// tables (ens_item_tile) and are not separated by block barriers: FP32 19,200 -> 19,530 MLUPS,
+// float-float 7,438 -> 7,443 (one barrier per tile with a refill for every tile: 19,520 and
+// 7,387).
 constexpr int ENS_CACHE = 64;
 
 template <class P, int TZ>
 __global__ void __launch_bounds__(TZ, ens_persistent_min_blocks<P, TZ>())
 k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, int total_items,
                  EnsControl* ctl, unsigned int* done, long long spin_limit, unsigned int extra_wait) {
-    __shared__ int sbase[Q];
+    __shared__ int tabs[2][Q];                 // pull-base tables of the item's tiles
     __shared__ unsigned int s_item, s_next;
     __shared__ int s_ok;
     __shared__ unsigned int s_seen[ENS_CACHE];
@@ -197,10 +238,9 @@ k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, in
         __syncthreads();
         if (s_item >= total || !s_ok) break;
         const int s = s_s, t0 = s_t0, t1 = s_t1;
-        for (int tl = t0; tl < t1; tl++) {
-            ens_tile<LoadCG>(s_L, tl, s, q, sbase);
-            __syncthreads();   // all stores of the tile issued; s_item, s_L, sbase may be reused
-        }
+        int col = -1, cur = 0;
+        for (int tl = t0; tl < t1; tl++) ens_item_tile<LoadCG>(s_L, tl, s, q, tabs, col, cur);
+        __syncthreads();   // all stores of the item issued; s_item, s_L and the tables may be reused
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(&done[s_i], (unsigned int)(t1 - t0));

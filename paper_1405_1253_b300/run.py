@@ -4,6 +4,9 @@ the adjoint step to a seeded random field at the final state (in the storage pre
   python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3 [--store moments]
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 3 --walls      (thermal walls)
+  python -m paper_1405_1253_b300.run --prec f64_ff --steps 20 --ensemble 16 --ens-mode 1
+      (the first 16 lattices of the 48-lattice ensemble: --steps steps in one launch per step
+       (--ens-mode 0) or one persistent launch (1), tile height 128)
 
 Used as the profiled program of the ncu summaries under profiles/.
 """
@@ -30,8 +33,25 @@ def main():
     ap.add_argument("--store", default="states", choices=["states", "moments"],
                     help="the adjoint reads the state (gathers f_t) or a moment record of the step")
     ap.add_argument("--walls", action="store_true", help="thermal walls at the bottom and top layer temperatures")
+    ap.add_argument("--ensemble", type=int, default=0, help="run the first N lattices of the 48-lattice ensemble")
+    ap.add_argument("--ens-mode", type=int, default=1, choices=[0, 1],
+                    help="0: one launch per step, 1: one persistent launch")
     args = ap.parse_args()
     from . import lbm
+    if args.ensemble > 0:
+        lats = W.ensemble_48()[:args.ensemble]
+        Ls = []
+        for d in lats:
+            Ls.append(lbm.Lattice(d.Lx, d.Lz, d.tau, d.grav, prec=args.prec))
+            Ls[-1].init_from(d)
+        ens = lbm.Ensemble(Ls)
+        ens.config(mode=args.ens_mode, tile_z=128)
+        ens.step(args.steps)
+        ens.sync()
+        mass = sum(L.global_sums()[0] for L in Ls)
+        print(json.dumps({"prec": args.prec, "ensemble": len(Ls), "sites": sum(d.sites for d in lats),
+                          "mode": args.ens_mode, "steps": args.steps, "mass": mass}))
+        return
     lat = W.Lattice(args.Lx, args.Lz, tau=args.tau, grav=args.grav, K=args.modes, sigma=args.sigma, seed=args.seed)
     L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=args.prec)
     L.init_from(lat)
