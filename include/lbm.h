@@ -284,10 +284,11 @@ int lbm_ensemble_create(lbm_ensemble **out, int n, lbm_ctx *const *ctxs);
 int lbm_ensemble_destroy(lbm_ensemble *e);
 
 /* Launch shape: mode 0 = one launch per step over the tiles of all lattices; mode 1 =
- * one persistent cooperative launch for all steps, CTAs taking (step, tile) items from
- * a step-major queue with a per-lattice step barrier (a tile of step s waits until all
- * tiles of step s-1 of its lattice are done).  tile_z: threads (rows) per tile, 64, 128
- * or 256.  ctas_per_sm: persistent CTAs per SM (0: as many as fit).                   */
+ * one persistent cooperative launch for all steps, CTAs taking work items (a step and 8
+ * consecutive tiles of one lattice) from a step-major queue with a per-lattice step
+ * barrier (an item of step s waits until all tiles of step s-1 of its lattice are done).
+ * tile_z: threads (rows) per tile, 64, 128 or 256.  ctas_per_sm: persistent CTAs per SM
+ * (0: as many as fit).                                                                */
 int lbm_ensemble_config(lbm_ensemble *e, int mode, int tile_z, int ctas_per_sm);
 
 /* Autotuner: times `steps` steps (after a warm-up of the same length) for every mode,
