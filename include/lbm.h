@@ -56,14 +56,22 @@ enum {
  *   LBM_F32     FP32 storage, FP32 collide arithmetic (compensated moment sums; the
  *               collide update is repaired to conserve mass, momentum + rho g and
  *               internal energy).
- *   value 2     reserved for FP32 storage of the deviation from a per-row FP64
- *               reference state; not built, rejected with LBM_EINVAL.
+ *   LBM_F32_DEV FP32 storage of the deviation d = f - fref(l, z) from a per-row
+ *               reference, fref = f^eq(rho0(z), gvec/2, T0(z)) at the horizontal means
+ *               rho0, T0 of the rows of the last lbm_init_layers state (of a uniform
+ *               rho = T = 1 state before it), kept by the context in FP64; FP32 collide
+ *               arithmetic on deviations only (the reference's moments per row from
+ *               FP64 tables).  The step, the state copies and the diagnostics take it;
+ *               thermal walls, the push form, lbm_propagate, the slabs, the ensembles and
+ *               every adjoint entry point return LBM_ESTATE for it, lbm_step_host
+ *               LBM_EINVAL (it takes FP64 storage).  The diagnostics work on an FP64 copy
+ *               of the state in a temporary device buffer (37*Lx*Lz doubles).
  *   LBM_F64_FF  IEEE binary64 storage; moments summed in 64-bit integers, the rest of
  *               the collide in float-float arithmetic (pairs of FP32 carrying a ~48-bit
  *               significand) on the FP32 and integer pipes, one FP64 FMA per population
  *               for the relaxation; same storage and bytes as LBM_F64, results equal to
  *               it to ~1e-14 per step.                                                 */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F64_FF = 3 } lbm_prec;
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_DEV = 2, LBM_F64_FF = 3 } lbm_prec;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque */
 

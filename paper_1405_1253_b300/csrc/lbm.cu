@@ -20,6 +20,7 @@
 #include "step_f64.cuh"
 #include "step_ff.cuh"
 #include "step_f32.cuh"
+#include "step_f32dev.cuh"
 #include "init_diag.cuh"
 #include "adjoint.cuh"
 #include "adjoint_ff.cuh"
@@ -214,9 +215,16 @@ struct lbm_ctx {
     int thermal = 0;
     ThermalWall tw{};
     double* gmu = nullptr;      // 6 * Q * Lx: ghost-pull scratch of the thermal-wall adjoint
+    // LBM_F32_DEV: the per-row reference (step_f32dev.cuh)
+    double* fref = nullptr;     // Q * Lz: fref_l(z) (FP64)
+    float* dref = nullptr;      // Q * Lz: gref_l(z) - fref_l(z)
+    float* rowc = nullptr;      // RC_N * Lz: per-row constants
 };
 
 static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
+static bool valid_prec(int prec) {
+    return prec == LBM_F64 || prec == LBM_F32 || prec == LBM_F32_DEV || prec == LBM_F64_FF;
+}
 
 static StepParams step_params(const lbm_ctx* c) {
     StepParams p;
@@ -247,7 +255,8 @@ static int ensure_part(lbm_ctx* c, size_t n) {
 
 static void free_ctx(lbm_ctx* c) {
     if (!c) return;
-    void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err, c->gmu};
+    void* ps[] = {c->zcol, c->modes, c->part, c->small, c->dLrow, c->colred, c->err, c->gmu,
+                  c->fref, c->dref, c->rowc};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; k++) {
@@ -260,7 +269,8 @@ static void free_ctx(lbm_ctx* c) {
     delete c;
 }
 
-// One step of the columns of tiling t in precision prec (p describes the buffers).
+// One step of the columns of tiling t in precision prec (p describes the buffers); not for
+// LBM_F32_DEV, whose step needs its context's reference (ctx_step).
 static void launch_step(int prec, const void* fin, void* fout, const StepParams& p, const Tiling& t,
                         cudaStream_t st) {
     switch (prec) {
@@ -273,6 +283,10 @@ static void launch_step(int prec, const void* fin, void* fout, const StepParams&
 // One step of context c from fin to fout with its wall rule (one launch either way).
 static void ctx_step(const lbm_ctx* c, const void* fin, void* fout, const StepParams& p, cudaStream_t st) {
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
+    if (c->prec == LBM_F32_DEV) {        // bounce-back walls only (lbm_set_walls)
+        launch_step_f32dev((const float*)fin, (float*)fout, fd_params(p, c->dref, c->rowc), t, st);
+        return;
+    }
     if (!c->thermal) {
         launch_step(c->prec, fin, fout, p, t, st);
         return;
@@ -292,16 +306,110 @@ static void ctx_step(const lbm_ctx* c, const void* fin, void* fout, const StepPa
     }
 }
 
+#define NOT_DEV(c, what)                                                                        \
+    do {                                                                                        \
+        if ((c)->prec == LBM_F32_DEV) return fail(LBM_ESTATE, what " is not available for LBM_F32_DEV"); \
+    } while (0)
+
 #define NEED_BOUNCE_BACK(c, what)                                                               \
     do {                                                                                        \
         if ((c)->thermal) return fail(LBM_ESTATE, what " supports the bounce-back walls only"); \
     } while (0)
 
 template <class S>
-static void launch_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int renorm) {
+static void launch_moments(lbm_ctx* c, const void* f, double* rho, double* ux, double* uz, double* T, int renorm) {
     dim3 grid((c->Lz + 127) / 128, c->Lx);
-    k_moments<S><<<grid, 128, 0, c->stream>>>((const typename S::T*)c->buf[c->cur], c->Lx, c->Lz, c->grav, renorm,
+    k_moments<S><<<grid, 128, 0, c->stream>>>((const typename S::T*)f, c->Lx, c->Lz, c->grav, renorm,
                                               rho, ux, uz, T);
+}
+
+// A diagnostic's view of the current state: the state itself, or (LBM_F32_DEV) its FP64
+// populations fref + d in a temporary buffer, released (stream-ordered) with the view.
+struct StateView {
+    const void* f = nullptr;
+    int prec = LBM_F64;
+    double* tmp = nullptr;
+    cudaStream_t st = nullptr;
+    StateView() = default;
+    StateView(const StateView&) = delete;
+    StateView& operator=(const StateView&) = delete;
+    ~StateView() {
+        if (tmp) cudaFreeAsync(tmp, st);
+    }
+};
+static int state_view(lbm_ctx* c, StateView& v) {
+    v.st = c->stream;
+    if (c->prec != LBM_F32_DEV) {
+        v.f = c->buf[c->cur];
+        v.prec = c->prec;
+        return LBM_OK;
+    }
+    const long long n = (long long)Q * c->Lx * c->Lz;
+    if (dev_malloc_async(&v.tmp, n * sizeof(double), c->stream) != cudaSuccess)
+        return fail(LBM_ENOMEM, "cannot allocate the FP64 view of the state (%lld doubles)", n);
+    k_to_f64_dev<<<(unsigned int)((n + 255) / 256), 256, 0, c->stream>>>((const float*)c->buf[c->cur], 0, n,
+                                                                      c->Lx * c->Lz, c->Lz, c->fref, v.tmp);
+    LAUNCH_CHECK();
+    v.f = v.tmp;
+    v.prec = LBM_F64;
+    return LBM_OK;
+}
+
+// Host equilibrium (closed form of the 4th-order Hermite expansion, long double) with the
+// library's quadrature: f[l] = w_l rho P(s, |u|^2, T - 1).
+static void feq_host(long double rho, long double ux, long double uz, long double T, long double (&f)[Q]) {
+    const long double r = g_quad.r, r2 = r * r, th = T - 1.0L, u2 = ux * ux + uz * uz;
+    for (int l = 0; l < Q; l++) {
+        const long double C2 = r2 * c2(l);
+        const long double s = r * (cx(l) * ux + cz(l) * uz);
+        const long double K0 = 1.0L - 0.5L * u2 + 0.5L * th * (C2 - 2.0L) + 0.125L * u2 * u2
+                             - 0.25L * th * u2 * (C2 - 4.0L) + 0.125L * th * th * (C2 * C2 - 8.0L * C2 + 8.0L);
+        const long double K1 = 1.0L - 0.5L * u2 + 0.5L * th * (C2 - 4.0L);
+        const long double K2 = 0.5L - 0.25L * u2 + 0.25L * th * (C2 - 6.0L);
+        const long double P = K0 + s * (K1 + s * (K2 + s * (1.0L / 6.0L + s / 24.0L)));
+        f[l] = (long double)g_quad.w_shell[shell_of(l)] * rho * P;
+    }
+}
+
+// LBM_F32_DEV: build the reference of rows with means rho0[z], T0[z] (host, long double) and
+// upload fref (FP64), dref and the per-row constants (FP32); see step_f32dev.cuh.  Blocks the
+// host until the copies are done.
+static int dev_reference(lbm_ctx* c, const double* rho0, const double* T0) {
+    const int Lz = c->Lz;
+    const long double r = g_quad.r, u0z = -0.5L * c->grav;
+    std::vector<long double> fr((size_t)Q * Lz);
+    for (int z = 0; z < Lz; z++) {
+        long double f[Q];
+        feq_host(rho0[z], 0.0L, u0z, T0[z], f);
+        for (int l = 0; l < Q; l++) fr[(size_t)l * Lz + z] = f[l];
+    }
+    std::vector<double> h_fref((size_t)Q * Lz);
+    std::vector<float> h_dref((size_t)Q * Lz), h_rowc((size_t)RC_N * Lz);
+    for (int z = 0; z < Lz; z++) {
+        long double R = 0, Jx = 0, Jz = 0, E = 0;
+        for (int l = 0; l < Q; l++) {
+            int ls = l, zs = z - cz(l);       // the pull source of population l at row z
+            if (zs < 0) { ls = opp(l); zs = cz(l) - 1 - z; }
+            else if (zs >= Lz) { ls = opp(l); zs = 2 * Lz - 1 - z + cz(l); }
+            const long double g = fr[(size_t)ls * Lz + zs];
+            h_fref[(size_t)l * Lz + z] = (double)fr[(size_t)l * Lz + z];
+            h_dref[(size_t)l * Lz + z] = (float)(g - fr[(size_t)l * Lz + z]);
+            R += g;
+            Jx += cx(l) * g;
+            Jz += cz(l) * g;
+            E += c2(l) * g;
+        }
+        const long double eg = E / R, ugx = r * Jx / R, ugz = r * Jz / R, ug2 = ugx * ugx + ugz * ugz;
+        const long double Tg = 0.5L * (r * r * eg - ug2);
+        const float v[RC_N] = {(float)rho0[z], (float)((long double)T0[z] - 1.0L), (float)(R - rho0[z]),
+                               (float)(Tg - T0[z]), (float)eg, (float)Jx, (float)Jz, (float)ug2};
+        for (int k = 0; k < RC_N; k++) h_rowc[(size_t)k * Lz + z] = v[k];
+    }
+    CU(cudaStreamSynchronize(c->stream));     // no step may read the tables while they change
+    CU(cudaMemcpy(c->fref, h_fref.data(), h_fref.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->dref, h_dref.data(), h_dref.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->rowc, h_rowc.data(), h_rowc.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return LBM_OK;
 }
 
 extern "C" {
@@ -361,8 +469,7 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     if (Lx < 1 || Lz < 6) return fail(LBM_EINVAL, "lattice %d x %d: need Lx >= 1, Lz >= 6", Lx, Lz);
     if ((long long)Q * Lx * Lz >= (1LL << 31))
         return fail(LBM_EINVAL, "lattice %d x %d too large: 37*Lx*Lz must be < 2^31", Lx, Lz);
-    if (prec != LBM_F64 && prec != LBM_F32 && prec != LBM_F64_FF)
-        return fail(LBM_EINVAL, "unknown precision %d", prec);
+    if (!valid_prec(prec)) return fail(LBM_EINVAL, "unknown precision %d", prec);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_EINVAL, "tau = %g must be > 0.5", tau);
     if (!(g >= 0.0) || !std::isfinite(g)) return fail(LBM_EINVAL, "g = %g must be >= 0", g);
     if (!buf0 || !buf1 || buf0 == buf1) return fail(LBM_EINVAL, "need two distinct device buffers");
@@ -395,6 +502,21 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess) {
         free_ctx(c);
         return fail(LBM_ECUDA, "memset of the error word failed");
+    }
+    if (prec == LBM_F32_DEV) {     // the reference of a uniform state until lbm_init_layers
+        ok = dev_malloc(&c->fref, (size_t)Q * Lz * sizeof(double)) == cudaSuccess &&
+             dev_malloc(&c->dref, (size_t)Q * Lz * sizeof(float)) == cudaSuccess &&
+             dev_malloc(&c->rowc, (size_t)RC_N * Lz * sizeof(float)) == cudaSuccess;
+        if (!ok) {
+            free_ctx(c);
+            return fail(LBM_ENOMEM, "reference table allocation failed");
+        }
+        const std::vector<double> one((size_t)Lz, 1.0);
+        rc = dev_reference(c, one.data(), one.data());
+        if (rc) {
+            free_ctx(c);
+            return rc;
+        }
     }
     *out = c;
     return LBM_OK;
@@ -474,6 +596,20 @@ int lbm_init_layers(lbm_ctx* c, const lbm_layers_desc* d) {
     LAUNCH_CHECK();
     dim3 grid((c->Lz + 127) / 128, c->Lx);
     void* f = c->buf[c->cur];
+    if (c->prec == LBM_F32_DEV) {      // reference of the initial rows, then the deviations
+        rc = ensure_part(c, 2 * (size_t)c->Lz);
+        if (rc) return rc;
+        k_init_rowmeans<<<c->Lz, 128, 0, c->stream>>>(c->zcol, ip, c->part);
+        LAUNCH_CHECK();
+        std::vector<double> h(2 * (size_t)c->Lz);
+        CU(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        rc = dev_reference(c, h.data(), h.data() + c->Lz);
+        if (rc) return rc;
+        k_init_dev<<<grid, 128, 0, c->stream>>>((float*)f, c->zcol, ip, c->fref);
+        LAUNCH_CHECK();
+        return LBM_OK;
+    }
     switch (c->prec) {
         case LBM_F64:
         case LBM_F64_FF:
@@ -495,6 +631,7 @@ int lbm_set_walls(lbm_ctx* c, int thermal, double T_bottom, double T_top) {
     if (thermal != 0 && thermal != 1) return fail(LBM_EINVAL, "thermal must be 0 or 1");
     if (thermal && !(T_bottom > 0.0 && T_top > 0.0 && std::isfinite(T_bottom) && std::isfinite(T_top)))
         return fail(LBM_EINVAL, "wall temperatures must be positive and finite");
+    if (thermal) NOT_DEV(c, "the thermal wall rule");
     if (thermal) {
         thermal_wall_q(quad_w_shell(), g_quad.r, T_bottom, 0, c->tw.q[0]);
         thermal_wall_q(quad_w_shell(), g_quad.r, T_top, 1, c->tw.q[1]);
@@ -520,6 +657,7 @@ int lbm_step_push(lbm_ctx* c, int nsteps) {
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     NEED_BOUNCE_BACK(c, "lbm_step_push");
+    NOT_DEV(c, "lbm_step_push");
     DeviceGuard dg(c->device);
     const StepParams p = step_params(c);
     const Tiling t = make_tiling(p.Lx, p.Lz, BLOCK_Z);
@@ -557,6 +695,7 @@ int lbm_step_chain(lbm_ctx* c, void* const* states, int n) {
 
 int lbm_propagate(lbm_ctx* c) {
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    NOT_DEV(c, "lbm_propagate");
     DeviceGuard dg(c->device);
     const Tiling t = make_tiling(c->Lx, c->Lz, BLOCK_Z);
     const void* fin = c->buf[c->cur];
@@ -594,12 +733,18 @@ static int convert_pops(lbm_ctx* c, double* buf, int on_device, bool to_f64) {
         double* dev = on_device ? buf + first : tmp;
         const int blocks = (int)((m + 255) / 256);
         if (to_f64) {
-            k_to_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
+            if (c->prec == LBM_F32_DEV)
+                k_to_f64_dev<<<blocks, 256, 0, c->stream>>>((const float*)f, first, m, (int)chunk, c->Lz, c->fref, dev);
+            else
+                k_to_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
             LAUNCH_CHECK();
             if (!on_device) CU(cudaMemcpyAsync(buf + first, tmp, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         } else {
             if (!on_device) CU(cudaMemcpyAsync(tmp, buf + first, m * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-            k_from_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
+            if (c->prec == LBM_F32_DEV)
+                k_from_f64_dev<<<blocks, 256, 0, c->stream>>>((float*)f, first, m, (int)chunk, c->Lz, c->fref, dev);
+            else
+                k_from_f64<StoreF32><<<blocks, 256, 0, c->stream>>>((float*)f, first, m, dev);
             LAUNCH_CHECK();
         }
         if (!on_device) CU(cudaStreamSynchronize(c->stream));
@@ -719,9 +864,15 @@ int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uz, double* T, int 
         k = 0;
         for (int i = 0; i < 4; i++) dev[i] = outs[i] ? tmp + (k++) * n : nullptr;
     }
-    switch (c->prec) {
-        case LBM_F64: case LBM_F64_FF: launch_moments<StoreF64>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
-        default: launch_moments<StoreF32>(c, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+    StateView v;
+    int rc = state_view(c, v);
+    if (rc) {
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+        return rc;
+    }
+    switch (v.prec) {
+        case LBM_F64: case LBM_F64_FF: launch_moments<StoreF64>(c, v.f, dev[0], dev[1], dev[2], dev[3], renormalised); break;
+        default: launch_moments<StoreF32>(c, v.f, dev[0], dev[1], dev[2], dev[3], renormalised); break;
     }
     LAUNCH_CHECK();
     if (!on_device) {
@@ -740,9 +891,12 @@ static int row_mean_device(lbm_ctx* c, double* Tbar_dev) {
     int rc = ensure_part(c, (size_t)nch * c->Lz);
     if (rc) return rc;
     dim3 grid((c->Lz + 127) / 128, nch);
-    const void* f = c->buf[c->cur];
+    StateView v;
+    rc = state_view(c, v);
+    if (rc) return rc;
+    const void* f = v.f;
     const int part_n = (int)std::min(c->part_cap, (size_t)INT_MAX);
-    switch (c->prec) {
+    switch (v.prec) {
         case LBM_F64: case LBM_F64_FF:
             k_rowT_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, nx_per, c->part, part_n); break;
         default:
@@ -795,10 +949,13 @@ int lbm_row_stats(lbm_ctx* c, double* T_mean, double* T_rms, double* Ek_mean, do
     double* means = c->part + (size_t)2 * nch * Lz;
     double* rms = means + 2 * (size_t)Lz;
     dim3 grid((Lz + 127) / 128, nch);
-    const void* f = c->buf[c->cur];
+    StateView v;
+    rc = state_view(c, v);
+    if (rc) return rc;
+    const void* f = v.f;
     for (int pass = 0; pass < 2; pass++) {
         const double* m = pass ? means : nullptr;
-        switch (c->prec) {
+        switch (v.prec) {
             case LBM_F64: case LBM_F64_FF:
                 k_row_stats_partial<StoreF64><<<grid, 128, 0, c->stream>>>((const double*)f, c->Lx, Lz, nx_per, c->grav, m, c->part);
                 break;
@@ -845,8 +1002,11 @@ int lbm_global_sums(lbm_ctx* c, double out[2]) {
     const int nblk = std::max(1, std::min(148 * 8, (nsite + RED_THREADS - 1) / RED_THREADS));
     int rc = ensure_part(c, 2 * (size_t)nblk);
     if (rc) return rc;
-    const void* f = c->buf[c->cur];
-    switch (c->prec) {
+    StateView v;
+    rc = state_view(c, v);
+    if (rc) return rc;
+    const void* f = v.f;
+    switch (v.prec) {
         case LBM_F64: case LBM_F64_FF:
             k_global_partial<StoreF64><<<nblk, RED_THREADS, 0, c->stream>>>((const double*)f, c->Lx, c->Lz, c->part); break;
         default:
@@ -895,6 +1055,7 @@ static int adjoint_walls_ready(lbm_ctx* c) {
 int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const void* lam_next, void* lam_out) {
     if (!c || !f_t || !lam_next || !lam_out) return fail(LBM_EINVAL, "NULL argument");
     if (lam_out == lam_next || lam_out == f_t) return fail(LBM_EINVAL, "lam_out must not alias the inputs");
+    NOT_DEV(c, "the adjoint step");
     DeviceGuard dg(c->device);
     int rc = adjoint_walls_ready(c);
     if (rc) return rc;
@@ -905,6 +1066,7 @@ int lbm_adjoint_step(lbm_ctx* c, const void* f_t, const void* lam_next, void* la
 
 int lbm_adjoint_chain(lbm_ctx* c, const void* const* states, int n, void* lam_a, void* lam_b, int* out_index) {
     if (!c || !states || !lam_a || !lam_b || !out_index) return fail(LBM_EINVAL, "NULL argument");
+    NOT_DEV(c, "the adjoint step");
     if (n < 0) return fail(LBM_EINVAL, "n < 0");
     if (lam_a == lam_b) return fail(LBM_EINVAL, "lam_a and lam_b must differ");
     for (int j = 0; j < n; j++) {
@@ -973,6 +1135,7 @@ int lbm_adjoint_chain_moments(lbm_ctx* c, const int64_t* const* moments, int n, 
 
 int lbm_loss_adjoint(lbm_ctx* c, const void* f, const double* dL_dTbar, void* lam_out) {
     if (!c || !f || !dL_dTbar || !lam_out) return fail(LBM_EINVAL, "NULL argument");
+    NOT_DEV(c, "the loss adjoint");
     DeviceGuard dg(c->device);
     CU(cudaMemcpyAsync(c->dLrow, dL_dTbar, (size_t)c->Lz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     dim3 grid((c->Lz + 127) / 128, c->Lx);
@@ -989,6 +1152,7 @@ int lbm_loss_adjoint(lbm_ctx* c, const void* f, const double* dL_dTbar, void* la
 int lbm_init_adjoint_full(lbm_ctx* c, const lbm_layers_desc* d, const void* lam0, double* dA_lo, double* dA_hi,
                           double* dph_lo, double* dph_hi) {
     if (!c || !lam0) return fail(LBM_EINVAL, "NULL argument");
+    NOT_DEV(c, "the initial-state adjoint");
     DeviceGuard dg(c->device);
     InitParams ip;
     int rc = fill_init_params(c, d, &ip);
@@ -1464,6 +1628,7 @@ int lbm_slabs_create(lbm_slabs** out, lbm_ctx* c, int nslab) {
     *out = nullptr;
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     NEED_BOUNCE_BACK(c, "the slab decomposition");
+    NOT_DEV(c, "the slab decomposition");
     if (nslab < 1 || c->Lx % nslab) return fail(LBM_EINVAL, "Lx = %d is not a multiple of nslab = %d", c->Lx, nslab);
     if (c->Lx / nslab < HX) return fail(LBM_EINVAL, "slabs of %d columns: need at least %d", c->Lx / nslab, HX);
     DeviceGuard dg(c->device);

@@ -24,8 +24,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 Q = 37
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ETIMEOUT, LBM_ENUMERIC, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PREC = {"f64": 0, "f32": 1, "f64_ff": 3}   # lbm_prec of include/lbm.h
-POP_BYTES = {"f64": 8, "f64_ff": 8, "f32": 4}
+PREC = {"f64": 0, "f32": 1, "f32_dev": 2, "f64_ff": 3}   # lbm_prec of include/lbm.h
+POP_BYTES = {"f64": 8, "f64_ff": 8, "f32": 4, "f32_dev": 4}
 
 _vp, _dp, _ip, _i, _d, _sz = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.c_int, ctypes.c_double, ctypes.c_size_t)

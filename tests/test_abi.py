@@ -56,17 +56,18 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
 
 
 def test_precision_numbering_matches_header(lib):
-    """The storage precisions keep the numbering the boundary fixes: LBM_F64 = 0 and
-    LBM_F32 = 1; value 2 (FP32 deviation storage) is reserved and refused; the
-    float-float FP64 form sits after it.  The binding's table must say the same."""
+    """The storage precisions keep the numbering the boundary fixes: LBM_F64 = 0,
+    LBM_F32 = 1 and LBM_F32_DEV = 2 (FP32 deviation storage); the float-float FP64 form
+    sits after them.  The binding's table must say the same, and other values are refused."""
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
     m = re.search(r"typedef enum \{([^}]*)\} lbm_prec;", src)
     assert m, "lbm_prec enum not found"
     vals = {k: int(v) for k, v in re.findall(r"(LBM_\w+)\s*=\s*(\d+)", m.group(1))}
-    assert vals == {"LBM_F64": 0, "LBM_F32": 1, "LBM_F64_FF": 3}
-    assert lib.PREC == {"f64": vals["LBM_F64"], "f32": vals["LBM_F32"], "f64_ff": vals["LBM_F64_FF"]}
+    assert vals == {"LBM_F64": 0, "LBM_F32": 1, "LBM_F32_DEV": 2, "LBM_F64_FF": 3}
+    assert lib.PREC == {"f64": vals["LBM_F64"], "f32": vals["LBM_F32"], "f32_dev": vals["LBM_F32_DEV"],
+                        "f64_ff": vals["LBM_F64_FF"]}
     ctx = ctypes.c_void_p()
-    for bad in (2, 4, -1):
+    for bad in (4, 5, -1):
         rc = lib._lib.lbm_create(ctypes.byref(ctx), 8, 16, bad, 0.8, 1e-4, None, None, 0, None)
         assert rc == lib.LBM_EINVAL and b"precision" in lib._lib.lbm_last_error()
         assert not ctx.value

@@ -1,0 +1,144 @@
+"""FP32 storage of the deviation from a per-row FP64 reference (LBM_F32_DEV) against the
+FP64 oracle.
+
+The stored value is d = f - fref(l, z) in FP32 and the collide rounds, in FP32, only
+quantities of the size of d or of the step's change (the O(1) parts come from FP64 tables),
+so each step adds an error of a few units of 2^-24 times |d| rather than times |f| as plain
+FP32 storage does.  On the three-layer workload |d| stays below ~15% of f at the interfaces
+(the layer temperatures differ by 5%, which the outer shells' populations amplify through
+the |c|^2 and |c|^4 terms of the equilibrium) and far below that in the layers; a reference
+of a uniform state (rho0 = T0 = 1) leaves |d| up to ~30% of f.  That bounds the error after
+100 steps by roughly 100 * 2^-24 * 0.15 ~ 1e-6 relative per population in the worst case; the
+tests ask for 1e-6 and, as the point of the storage, for at least five times less error than
+plain FP32 storage on the same inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_1253_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_100 = 1e-6       # max relative error per population after 100 steps (see above)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1405_1253_b300 import lbm as m
+    return m
+
+
+def oracle_init(lat):
+    return oracle.init_layers(lat.Lx, lat.Lz, **lat.layer_args())
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def make(lbm, lat, prec):
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
+    L.init_from(lat)
+    return L
+
+
+def test_init_matches_oracle(lbm):
+    """f = fref + d with d rounded once to FP32: error <= 2^-24 |d| <= 2^-24 * 30% of f."""
+    lat = W.PARITY_64x128
+    L = make(lbm, lat, "f32_dev")
+    err = max_rel(L.populations(), oracle_init(lat))
+    print("f32_dev init error", err)
+    assert err < 2e-8
+
+
+def test_step_parity_100_steps(lbm):
+    lat = W.PARITY_64x128
+    ref = oracle.step(oracle_init(lat), lat.tau, lat.grav, W.PARITY_STEPS)
+    errs = {}
+    for prec in ("f32_dev", "f32"):
+        L = make(lbm, lat, prec)
+        L.step(W.PARITY_STEPS)
+        L.sync()
+        errs[prec] = max_rel(L.populations(), ref)
+        L.close()
+    print("100-step errors", errs)
+    assert errs["f32_dev"] < TOL_100
+    assert errs["f32_dev"] < errs["f32"] / 5
+
+
+@pytest.mark.parametrize("Lx,Lz", [(1, 6), (2, 7), (3, 37), (5, 131), (4, 200), (7, 260)])
+def test_step_parity_edge_shapes(lbm, Lx, Lz):
+    """Smallest lattices, x wrap at Lx < 3, ragged z tails, wall rows on both sides of a
+    short column; the state is set directly, so the reference is the context's uniform one
+    (rho0 = T0 = 1) and |d| reaches ~30% of f.  Per step the error is up to ~16 units of
+    2^-24 |d| / f: the FP32 sums of the 37 pulled deviations set T - T0, which the outer
+    shells' equilibria amplify about sixfold (d f^eq / dT ~ (r^2 |c|^2 - 2) / 2 f^eq), on top of
+    the roundings of the update; 5 steps: 5 * 16 * 2^-24 * 0.3 = 1.4e-6."""
+    rng = np.random.default_rng(Lx * 1000 + Lz)
+    lat = W.Lattice(Lx, Lz, tau=0.7, grav=2e-4, K=2, sigma=0.5, seed=7)
+    f0 = oracle_init(lat) * (1 + 1e-3 * rng.standard_normal((37, Lx, Lz)))
+    L = lbm.Lattice(Lx, Lz, lat.tau, lat.grav, prec="f32_dev")
+    L.set_populations(f0)
+    L.step(5)
+    ref = oracle.step(f0, lat.tau, lat.grav, 5)
+    err = max_rel(L.populations(), ref)
+    print("edge", Lx, Lz, err)
+    assert err < 1.4e-6
+
+
+def test_set_get_round_trip(lbm):
+    """set_populations stores (float)(f - fref): reading back is exact to 2^-24 |f - fref|,
+    and |f - fref| stays below ~30% of f."""
+    lat = W.PARITY_64x128
+    L = make(lbm, lat, "f32_dev")
+    rng = np.random.default_rng(3)
+    f1 = oracle_init(lat) * (1 + 1e-4 * rng.standard_normal((37, lat.Lx, lat.Lz)))
+    L.set_populations(f1)
+    err = max_rel(L.populations(), f1)
+    print("round trip", err)
+    assert err < 2.0 ** -24 * 0.3
+
+
+def test_mass_and_diagnostics(lbm):
+    """Mass is kept to the FP32 rounding of the deviations (no conservation repair: measured
+    ~5e-12 relative per step, against ~7e-11 for plain FP32 storage with its repair) over 500
+    steps, and the
+    diagnostics (on an FP64 copy of the state) agree with an FP64 context holding the same
+    populations."""
+    lat = W.PARITY_64x128
+    L = make(lbm, lat, "f32_dev")
+    m0 = L.global_sums()[0]
+    L.step(500)
+    m1 = L.global_sums()[0]
+    print("f32_dev mass drift over 500 steps", abs(m1 - m0) / m0)
+    assert abs(m1 - m0) / m0 < 1e-8
+    f = L.populations()
+    D = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f64")
+    D.set_populations(f)
+    for a, b in zip(L.moments(), D.moments()):
+        assert np.allclose(a, b, rtol=1e-14, atol=1e-16)
+    assert np.allclose(L.row_mean_T(), D.row_mean_T(), rtol=1e-14, atol=0)
+    assert np.allclose(L.widths(lat.T_u, lat.T_m, lat.T_d), D.widths(lat.T_u, lat.T_m, lat.T_d), rtol=1e-12)
+    assert np.allclose(L.global_sums(), D.global_sums(), rtol=1e-14)
+
+
+def test_refusals(lbm):
+    """What the deviation storage does not support answers LBM_ESTATE (LBM_EINVAL for the
+    host stepping, which takes FP64 storage), and the context stays usable."""
+    lat = W.PARITY_64x128
+    L = make(lbm, lat, "f32_dev")
+    f = L.current()
+    lam = f.clone()
+    out = f.clone()
+    calls = [lambda: L.adjoint_step(f, lam, out), lambda: L.step_push(1), lambda: L.propagate(),
+             lambda: L.set_walls(True, lat.T_d, lat.T_u), lambda: lbm.Slabs(L, 2),
+             lambda: L.adjoint_chain([f, f], lam, out)]
+    for call in calls:
+        with pytest.raises(lbm.LBMError) as e:
+            call()
+        assert e.value.code == lbm.LBM_ESTATE
+    L.set_walls(False)
+    L.step(2)
+    L.sync()
+    assert np.all(np.isfinite(L.populations()))
