@@ -217,7 +217,7 @@ struct lbm_ctx {
     double* gmu = nullptr;      // 6 * Q * Lx: ghost-pull scratch of the thermal-wall adjoint
     // LBM_F32_DEV: the per-row reference (step_f32dev.cuh)
     double* fref = nullptr;     // Q * Lz: fref_l(z) (FP64)
-    float* dref = nullptr;      // Q * Lz: gref_l(z) - fref_l(z)
+    float* dref = nullptr;      // NDREF * Lz: gref_l(z) - fref_l(z) by (shell, c_z) class
     float* rowc = nullptr;      // RC_N * Lz: per-row constants
 };
 
@@ -384,7 +384,7 @@ static int dev_reference(lbm_ctx* c, const double* rho0, const double* T0) {
         for (int l = 0; l < Q; l++) fr[(size_t)l * Lz + z] = f[l];
     }
     std::vector<double> h_fref((size_t)Q * Lz);
-    std::vector<float> h_dref((size_t)Q * Lz), h_rowc((size_t)RC_N * Lz);
+    std::vector<float> h_dref((size_t)NDREF * Lz), h_rowc((size_t)RC_N * Lz);
     for (int z = 0; z < Lz; z++) {
         long double R = 0, Jx = 0, Jz = 0, E = 0;
         for (int l = 0; l < Q; l++) {
@@ -393,7 +393,7 @@ static int dev_reference(lbm_ctx* c, const double* rho0, const double* T0) {
             else if (zs >= Lz) { ls = opp(l); zs = 2 * Lz - 1 - z + cz(l); }
             const long double g = fr[(size_t)ls * Lz + zs];
             h_fref[(size_t)l * Lz + z] = (double)fr[(size_t)l * Lz + z];
-            h_dref[(size_t)l * Lz + z] = (float)(g - fr[(size_t)l * Lz + z]);
+            if (dref_slot(l) >= 0) h_dref[(size_t)dref_slot(l) * Lz + z] = (float)(g - fr[(size_t)l * Lz + z]);
             R += g;
             Jx += cx(l) * g;
             Jz += cz(l) * g;
@@ -505,7 +505,7 @@ int lbm_create(lbm_ctx** out, int Lx, int Lz, int prec, double tau, double g, vo
     }
     if (prec == LBM_F32_DEV) {     // the reference of a uniform state until lbm_init_layers
         ok = dev_malloc(&c->fref, (size_t)Q * Lz * sizeof(double)) == cudaSuccess &&
-             dev_malloc(&c->dref, (size_t)Q * Lz * sizeof(float)) == cudaSuccess &&
+             dev_malloc(&c->dref, (size_t)NDREF * Lz * sizeof(float)) == cudaSuccess &&
              dev_malloc(&c->rowc, (size_t)RC_N * Lz * sizeof(float)) == cudaSuccess;
         if (!ok) {
             free_ctx(c);

@@ -29,19 +29,50 @@ namespace lbm {
 // velocity.
 enum { RC_RHO0 = 0, RC_TH0, RC_CRHO, RC_CT, RC_EG, RC_JGX, RC_JGZ, RC_UG2, RC_N };
 
+// dref_l(z) depends on l only through its shell and c_z (fref is the equilibrium at a row
+// state with no horizontal velocity, and a wall mirrors a population into opp(l) of the same
+// shell): it is zero for c_z = 0 (pulled from the same row) and takes 18 values per row for
+// the other 28 populations.  dref_slot(l): the table column of population l, -1 for c_z = 0.
+struct DrefSlots {
+    int slot[Q];
+    int n;
+};
+__host__ __device__ constexpr DrefSlots make_dref_slots() {
+    DrefSlots r{};
+    int keys[Q] = {};
+    int nk = 0;
+    for (int l = 0; l < Q; l++) {
+        r.slot[l] = -1;
+        if (cz(l) == 0) continue;
+        const int key = shell_of(l) * 8 + cz(l) + 3;
+        for (int j = 0; j < nk; j++)
+            if (keys[j] == key) r.slot[l] = j;
+        if (r.slot[l] < 0) {
+            keys[nk] = key;
+            r.slot[l] = nk++;
+        }
+    }
+    r.n = nk;
+    return r;
+}
+__host__ __device__ constexpr int dref_slot(int l) { return make_dref_slots().slot[l]; }
+constexpr int NDREF = make_dref_slots().n;
+static_assert(NDREF == 18, "18 distinct (shell, c_z) classes with c_z != 0");
+
 struct StepParamsFD {
     int Lx, Lz, plane;
     float omega, one_m_omega, us_z, T_shift, u0z;   // u0z = -g / 2
-    const float* __restrict__ dref;   // Q * Lz: dref_l(z) at l * Lz + z
+    const float* __restrict__ dref;   // NDREF * Lz: dref of slot k (dref_slot) at k * Lz + z
     const float* __restrict__ rowc;   // RC_N * Lz
 };
 
 template <bool WALL, class LD>
 __device__ __forceinline__ void site_f32dev(const float* __restrict__ fin, float* __restrict__ fout,
                                            const SiteAddr& ad, const StepParamsFD& p) {
+    const int z = ad.z, Lz = p.Lz;
+    const float* __restrict__ dref = p.dref + z;
     float d[Q];
     load_site<false, WALL, LD>(fin, ad, d);
-    const int z = ad.z, Lz = p.Lz;
     // -- moments: the pulled reference's (per row) plus the sums of the pulled deviations --
     float dR = d[0], dJx = 0.f, dJz = 0.f, dE = 0.f;
     static_for<NPAIR>([&](auto k) {
@@ -87,12 +118,11 @@ __device__ __forceinline__ void site_f32dev(const float* __restrict__ fin, float
     const float e20 = -0.25f * dq - 1.5f * dth, e21 = 0.25f * r2 * dth;
     const float a = r * ux, b = r * usz, b0 = r * p.u0z, db = r * duz;
     const float W = rho, V = drho;                                     // times w_shell below
-    const float* __restrict__ dref = p.dref + z;
     const int o = ad.dst();
-    {   // rest population: s = s0 = 0
+    {   // rest population: s = s0 = 0, dref = 0
         const float w0 = d_lat.wf[0];
         const float F = w0 * fmaf(W, e00, V * (1.f + d00_0));
-        const float v = fmaf(p.one_m_omega, d[0] + dref[0], p.omega * F);
+        const float v = fmaf(p.one_m_omega, d[0], p.omega * F);
         fout[LBM_IDX(o, Q * ad.plane)] = v;
     }
     static_for<NPAIR>([&](auto k) {
@@ -119,8 +149,14 @@ __device__ __forceinline__ void site_f32dev(const float* __restrict__ fin, float
         const float wsh = d_lat.wf[shell_of(A)];
         const float FA = wsh * fmaf(W, dEv + dOd, V * (Ev0 + Od0));
         const float FB = wsh * fmaf(W, dEv - dOd, V * (Ev0 - Od0));
-        const float vA = fmaf(p.one_m_omega, d[A] + dref[A * Lz], p.omega * FA);
-        const float vB = fmaf(p.one_m_omega, d[B] + dref[B * Lz], p.omega * FB);
+        float gA = d[A], gB = d[B];
+        if constexpr (cz(A) != 0) {
+            constexpr int SA = dref_slot(A), SB = dref_slot(B);
+            gA += dref[SA * Lz];
+            gB += dref[SB * Lz];
+        }
+        const float vA = fmaf(p.one_m_omega, gA, p.omega * FA);
+        const float vB = fmaf(p.one_m_omega, gB, p.omega * FB);
         fout[LBM_IDX(A * ad.plane + o, Q * ad.plane)] = vA;
         fout[LBM_IDX(B * ad.plane + o, Q * ad.plane)] = vB;
     });
@@ -136,8 +172,12 @@ __device__ __forceinline__ void tile_f32dev(const float* __restrict__ fin, float
     else site_f32dev<false, LD>(fin, fout, ad, p);
 }
 
-// Launched as a programmatic dependent of the previous kernel (as k_step_f32).
-__global__ void __launch_bounds__(BLOCK_Z)
+// Launched as a programmatic dependent of the previous kernel (as k_step_f32).  6 resident
+// blocks per SM (80 registers).  Measured on 1024 x 2048: with the full 37-column offset
+// table, 0.1478 ms at the unconstrained 92 registers (5 blocks), 0.1387 / 0.1364 / 0.1413 at
+// 6 / 7 / 8 blocks; the 18-column table then took 7 blocks to 0.1290 (an L1 prefetch of its
+// lines at the start of the site: 0.1360), and 6 / 8 blocks give 0.1283 / 0.1334.
+__global__ void __launch_bounds__(BLOCK_Z, 6)
 k_step_f32dev(const float* __restrict__ fin, float* __restrict__ fout, const __grid_constant__ StepParamsFD p,
               Tiling t) {
     pdl_allow_next();

@@ -20,7 +20,7 @@ from . import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--prec", default="f64_ff", choices=["f64", "f64_ff", "f32"])
+    ap.add_argument("--prec", default="f64_ff", choices=["f64", "f64_ff", "f32", "f32_dev"])
     ap.add_argument("--Lx", type=int, default=1024)
     ap.add_argument("--Lz", type=int, default=2048)
     ap.add_argument("--tau", type=float, default=0.7)
