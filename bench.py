@@ -35,9 +35,9 @@ Q = 37
 METRIC = "MLUPS and % HBM roofline, FP64 vs FP32-storage (stated error), adjoint/forward"
 REF_BUDGET_S = 120.0        # oracle seconds of one reference-arm run (warmup + timed steps)
 SPEC_HBM_GBS = 7700.0       # nominal B300 HBM3e bandwidth (context beside the measured copy peak)
-BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4}
-ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32"}
-KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32"}
+BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4, "f32_dev": 4}
+ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32", "f32_dev": "f32"}
+KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32", "f32_dev": "k_step_f32dev"}
 
 
 def measured_peaks():
@@ -267,16 +267,17 @@ def time_variant(torch, lbm, lat, prec, steps, warmup, stream):
 
 def bench_precision(torch, lbm, steps, stream):
     """The precision configuration: 4096 x 8192 (33.6 M sites, 128 modes), `steps` steps of
-    the FP32-storage step and of the FP64-accurate (float-float) step from the same seeded
-    initial state; relative L2 errors of rho and T and relative errors of both fronts' widths
-    of the FP32 run against the FP64-accurate one, the mass drift, and the throughput of each
-    (CUDA events around the stepping only; ~222 waves of blocks per launch against ~14 on
-    1024 x 2048)."""
+    the FP64-accurate (float-float) step, the FP32-storage step and the FP32 deviation-storage
+    step from the same seeded initial state; relative L2 errors of rho and T and relative
+    errors of both fronts' widths of each FP32 run against the FP64-accurate one (FP32 storage
+    at the top level, deviation storage under f32_dev_errors), the mass drift, and the
+    throughput of each (CUDA events around the stepping only; ~222 waves of blocks per launch
+    against ~14 on 1024 x 2048)."""
     lat = W.PRECISION_4096x8192
     peak = float(measured_peaks()[0].get("hbm_gbs", 6400.0))
     out = {"workload": f"{lat.Lx}x{lat.Lz}, {steps} steps, tau={lat.tau}, g={lat.grav}, {lat.K} modes (seed {lat.seed})"}
     fields = {}
-    for prec in ("f64_ff", "f32"):
+    for prec in ("f64_ff", "f32", "f32_dev"):
         L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
         L.init_from(lat)
         m0 = L.global_sums()[0]
@@ -296,14 +297,22 @@ def bench_precision(torch, lbm, steps, stream):
         out[prec] = {"ms_per_step": ms, "mlups": lat.sites / (ms * 1e-3) / 1e6, "gbs": gbs, "hbm_frac": gbs / peak,
                      "widths": [float(v) for v in widths], "mass_rel_drift": float(abs(m1 - m0) / m0)}
         fields[prec] = (rho, T, widths)
-    (r64, T64, w64), (r32, T32, w32) = fields["f64_ff"], fields["f32"]
-    out["rho_rel_l2"] = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
-    out["T_rel_l2"] = float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64))
-    out["T_max_abs"] = float(np.abs(T32 - T64).max())
-    out["width_rel_err"] = [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]
-    out["speedup_f32"] = out["f64_ff"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    (r64, T64, w64) = fields["f64_ff"]
+    for low in ("f32", "f32_dev"):
+        r32, T32, w32 = fields[low]
+        err = {"rho_rel_l2": float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64)),
+               "T_rel_l2": float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64)),
+               "T_max_abs": float(np.abs(T32 - T64).max()),
+               "width_rel_err": [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]}
+        if low == "f32":      # the FP32-storage figures at the top level, as before
+            out.update(err)
+        else:
+            out["f32_dev_errors"] = err
+        out["speedup_" + low] = out["f64_ff"]["ms_per_step"] / out[low]["ms_per_step"]
     out["error_bound"] = 1e-5
     out["fields_within_bound"] = bool(out["rho_rel_l2"] < 1e-5 and out["T_rel_l2"] < 1e-5)
+    out["f32_dev_fields_within_bound"] = bool(out["f32_dev_errors"]["rho_rel_l2"] < 1e-5 and
+                                              out["f32_dev_errors"]["T_rel_l2"] < 1e-5)
     return out
 
 
@@ -522,22 +531,29 @@ def bench_walls(torch, lbm, lat, steps, stream):
 
 
 def fp32_error(torch, lbm, lat, steps, stream):
-    """Relative L2 error of rho and T of the FP32-storage step against the FP64-accurate
-    step after `steps` steps from the same initial state."""
+    """Relative L2 error of rho and T of the FP32-storage step (top level) and of the FP32
+    deviation-storage step (f32_dev) against the FP64-accurate step after `steps` steps from
+    the same initial state."""
     out = {}
     fields = {}
-    for prec in ("f64_ff", "f32"):
+    for prec in ("f64_ff", "f32", "f32_dev"):
         L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=stream)
         L.init_from(lat)
         L.step(steps)
         rho, _, _, T = L.moments()
         fields[prec] = (rho, T, L.widths(lat.T_u, lat.T_m, lat.T_d))
         L.close()
-    (r64, T64, w64), (r32, T32, w32) = fields["f64_ff"], fields["f32"]
     out["steps"] = steps
-    out["rho_rel_l2"] = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
-    out["T_rel_l2"] = float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64))
-    out["width_rel_err"] = [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]
+    r64, T64, w64 = fields["f64_ff"]
+    for low in ("f32", "f32_dev"):
+        r32, T32, w32 = fields[low]
+        err = {"rho_rel_l2": float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64)),
+               "T_rel_l2": float(np.linalg.norm(T32 - T64) / np.linalg.norm(T64)),
+               "width_rel_err": [float(abs(a - b) / abs(b)) for a, b in zip(w32, w64)]}
+        if low == "f32":
+            out.update(err)
+        else:
+            out["f32_dev"] = err
     return out
 
 
@@ -607,7 +623,7 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants:
-        for v in ("f64_ff", "f64", "f32"):
+        for v in ("f64_ff", "f64", "f32", "f32_dev"):
             vsteps = 10 if v == "f64" else 20
             vms = time_variant(torch, lbm, lat, v, vsteps, 3, stream)
             vbytes = 2 * Q * BYTES_PER_POP[v] * sites
@@ -685,7 +701,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["f64_ff", "f64", "f32"], default="f64_ff")
+    ap.add_argument("--prec", choices=["f64_ff", "f64", "f32", "f32_dev"], default="f64_ff")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
