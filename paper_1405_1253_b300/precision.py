@@ -1,6 +1,7 @@
-"""FP32-storage step against the FP64-accurate step on the same seeded initial state.
+"""FP32-storage step (or, --low f32_dev, FP32 storage of the deviation from the per-row
+reference) against the FP64-accurate step on the same seeded initial state.
 
-  python -m paper_1405_1253_b300.precision [--Lx 4096 --Lz 8192 --steps 2000]
+  python -m paper_1405_1253_b300.precision [--Lx 4096 --Lz 8192 --steps 2000] [--low f32_dev]
 
 Prints one JSON line: relative L2 errors of rho and T, relative errors of both fronts'
 mixing widths, the maximum over sites of |T32 - T64|, and the time of each run (CUDA
@@ -39,7 +40,7 @@ def main():
     ap.add_argument("--Lx", type=int, default=W.PRECISION_4096x8192.Lx)
     ap.add_argument("--Lz", type=int, default=W.PRECISION_4096x8192.Lz)
     ap.add_argument("--steps", type=int, default=W.PRECISION_STEPS)
-    ap.add_argument("--low", default="f32", choices=["f32"])
+    ap.add_argument("--low", default="f32", choices=["f32", "f32_dev"])
     args = ap.parse_args()
     import torch
     from . import lbm
