@@ -53,6 +53,7 @@ KERNEL_SOURCES = {
     "k_step_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh"),
     "k_step_f64": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_f64.cuh"),
     "k_step_f32": ("lattice.cuh", "common.cuh", "step_f32.cuh"),
+    "k_step_f32dev": ("lattice.cuh", "common.cuh", "init_diag.cuh", "step_f32dev.cuh"),
     "k_adjoint_ff": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
     "k_adjoint_ff_moments": ("lattice.cuh", "common.cuh", "ff.cuh", "moments_fix.cuh", "step_ff.cuh", "adjoint_ff.cuh"),
 }
