@@ -365,17 +365,21 @@ def bench_ensemble(torch, lbm, prec, steps, stream, tune_steps=20):
 def bench_adjoint(torch):
     """Gradient workload: 256x512, 2000 steps, checkpoint every 100: forward and backward
     (recompute + adjoint) wall times and device memory, for the three backward stores of the
-    float-float driver (recomputed moment records, with the recompute of the next segment
-    overlapping the adjoint of the current one on a second stream and without; moment records
-    taped in the forward; segment states) and for an FP32-storage run."""
+    float-float driver (recomputed moment records, with the recompute of earlier segments
+    overlapping the adjoint of the current one on a second stream, four record sets (the
+    default) or two, and without the overlap; moment records taped in the forward; segment
+    states) and for an FP32-storage run."""
     from paper_1405_1253_b300 import adjoint
     lat = W.GRADIENT_256x512
     out = {"workload": "256x512, 2000 steps, checkpoint every 100, 16 modes per front (f64_ff)"}
     m = lat.modes()
-    for key, store, prec, pipe in (("moments", "moments", "f64_ff", True), ("moments_serial", "moments", "f64_ff", False),
-                                   ("tape", "tape", "f64_ff", False), ("states", "states", "f64_ff", False),
-                                   ("f32", "states", "f32", False)):
-        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store, pipeline=pipe)
+    for key, store, prec, pipe, nset in (("moments", "moments", "f64_ff", True, None),
+                                         ("moments_2sets", "moments", "f64_ff", True, 2),
+                                         ("moments_serial", "moments", "f64_ff", False, None),
+                                         ("tape", "tape", "f64_ff", False, None), ("states", "states", "f64_ff", False, None),
+                                         ("f32", "states", "f32", False, None)):
+        drv = adjoint.WidthGradient(lat, W.GRADIENT_STEPS, W.GRADIENT_CKPT, prec=prec, store=store, pipeline=pipe,
+                                    record_sets=nset)
         drv.forward(m.amp_lo, m.amp_hi)      # warm
         drv.backward()
         drv.forward(m.amp_lo, m.amp_hi)
@@ -384,12 +388,16 @@ def bench_adjoint(torch):
         drv.close()
         mem = st.checkpoint_bytes + st.segment_bytes + 2 * st.state_bytes
         out[key] = {"forward_s": st.forward_s, "backward_s": st.backward_s,
+                      "record_sets": len(getattr(drv, "moms_sets", [])) or None,
+                      "recomputed_steps": st.recompute_steps,
                       "backward_over_forward": st.backward_s / st.forward_s,
                       "memory_bytes": mem, "forward_memory_bytes": 2 * st.state_bytes,
                       "memory_over_forward": mem / (2 * st.state_bytes),
                       "grad_norm": float(np.sqrt((g_lo ** 2).sum() + (g_hi ** 2).sum()))}
-    # the tape's forward also writes the moment records: its backward against the plain forward too
-    out["tape"]["backward_over_plain_forward"] = out["tape"]["backward_s"] / out["moments"]["forward_s"]
+    # the tape's and the moment stores' forwards also write moment records: their backward
+    # against the plain checkpointed forward (the state store's) too
+    for key in ("tape", "moments", "moments_2sets", "moments_serial"):
+        out[key]["backward_over_plain_forward"] = out[key]["backward_s"] / out["states"]["forward_s"]
     return out
 
 def bench_slabs(torch, lbm, lat, steps, stream, prec="f64_ff"):

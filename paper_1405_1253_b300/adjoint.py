@@ -11,11 +11,13 @@ adjoint of the initial state finally gives dL/dA.  Every step runs in the CUDA l
 this module only orders the calls and owns the buffers (through PyTorch).
 
 Memory: (N/K) checkpoints and 2 adjoint fields, each 37 Lx Lz doubles, and per segment either
-(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through (two sets
-of records when the recompute of the next segment overlaps the adjoint of the current one on a
-second stream, the default).  The "tape" store instead records the moments of all N steps
-during the forward pass (32 bytes per site and step, no checkpoints), so the backward
-recomputes nothing.
+(K - 1) states or K moment records of 4 Lx Lz int64 plus two states to step through (with the
+moment records: `record_sets` sets of K records, by default four when the recompute of earlier
+segments overlaps the adjoint of the current one on a second stream and one without; the
+forward records the moments of its last `record_sets` segments into them directly, so the
+backward recomputes only the segments before those).  The "tape" store instead records the
+moments of all N steps during the forward pass (32 bytes per site and step, no checkpoints),
+so the backward recomputes nothing.
 """
 from __future__ import annotations
 
@@ -52,12 +54,15 @@ class WidthGradient:
     forward records the moments of every step (N x 32 bytes per site; ckpt only sets the
     length of each adjoint chain call) and the backward runs the adjoint steps alone.
     walls=(T_bottom, T_top): thermal walls (lbm_set_walls) in the forward and the adjoint
-    (f64_ff, states).  pipeline (store "moments"): the recompute of segment s - 1 runs on a
-    second stream while the adjoint chain of segment s runs (two sets of records); the
-    gradient is the same bit for bit."""
+    (f64_ff, states).  pipeline (store "moments"): the recompute of earlier segments runs on a
+    second stream while the adjoint chain of segment s runs; record_sets (store "moments"):
+    the sets of K moment records, at least 2 with the pipeline (default 4) and 1 without
+    (default 1); the recompute of segment r refills set r % record_sets after the adjoint of
+    r + record_sets has read it, and the forward records its last record_sets segments itself.
+    Every store and setting gives the same gradient bit for bit."""
 
     def __init__(self, lat: LatticeDesc, nsteps: int, ckpt: int, prec: str = "f64_ff", store: str = None,
-                 walls=None, pipeline: bool = True):
+                 walls=None, pipeline: bool = True, record_sets: int = None):
         import torch
         if nsteps < 1 or ckpt < 1 or nsteps % ckpt:
             raise ValueError("nsteps must be a positive multiple of ckpt")
@@ -73,6 +78,7 @@ class WidthGradient:
                 self.store != "states" and (prec != "f64_ff" or walls)):
             raise ValueError("store is 'states', or 'moments' / 'tape' with prec 'f64_ff' and bounce-back walls")
         self.pipeline = False
+        self.n_taped = 0
         self.L = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec)
         if walls is not None:                      # thermal walls at (T_bottom, T_top)
             self.L.set_walls(True, *walls)
@@ -95,12 +101,17 @@ class WidthGradient:
             # pipeline, two sets of records: the recompute of segment s - 1 (a second context on
             # a second stream) fills one while the adjoint chain of segment s reads the other
             self.pipeline = bool(pipeline) and self.N // self.K > 1
-            nset = 2 if self.pipeline else 1
+            nset = record_sets if record_sets is not None else (4 if self.pipeline else 1)
+            if nset < (2 if self.pipeline else 1):
+                raise ValueError("record_sets must be at least 2 with the pipeline, 1 without")
             self.moms_sets = [torch.empty((self.K, 4 * lat.Lx * lat.Lz), dtype=torch.int64, device=dev)
                               for _ in range(nset)]
             self.moms = self.moms_sets[0]
             self.work = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
             seg_bytes = nset * self.moms.numel() * 8 + 2 * 8 * n
+            # the forward records the moments of its last segments straight into the record
+            # sets (one per set), so that the backward's first adjoint chains need no recompute
+            self.n_taped = min(nset, self.N // self.K)
             if self.pipeline:
                 self.rec_stream = torch.cuda.Stream(device=dev)
                 self.Lrec = _lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec=prec, stream=self.rec_stream)
@@ -134,9 +145,19 @@ class WidthGradient:
             self.L.record_moments(self.L.current(), self.work[0], self.work[1], list(self.moms))
             self.L.current().copy_(self.work[(self.N - 1) % 2])
         else:
-            for s in range(self.N // self.K):
-                self.ckpts[s].copy_(self.L.current())
-                self.L.step(self.K)
+            S = self.N // self.K
+            for s in range(S):
+                if s >= S - self.n_taped:
+                    # a segment the backward reads first: its K steps recording their moments
+                    # into the record set the backward's adjoint chain of s reads (the same
+                    # arithmetic as the plain step, so the same states bit for bit)
+                    sets = self.moms_sets
+                    self.L.record_moments(self.L.current(), self.work[0], self.work[1],
+                                          list(sets[s % len(sets)]))
+                    self.L.current().copy_(self.work[(self.K - 1) % 2])
+                else:
+                    self.ckpts[s].copy_(self.L.current())
+                    self.L.step(self.K)
         widths, dL = self.L.widths(lat.T_u, lat.T_m, lat.T_d, with_grad=True)
         self.stats.forward_s = time.perf_counter() - t0
         self.stats.widths = widths
@@ -154,6 +175,7 @@ class WidthGradient:
             raise RuntimeError("backward before forward")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        self.stats.recompute_steps = self.stats.adjoint_steps = 0    # counts of this backward
         cur, nxt = self.lam
         self.L.loss_adjoint(self._fN, self._dL * float(grad_out), cur)
         segments = range(self.N // self.K - 1, -1, -1)
@@ -172,10 +194,13 @@ class WidthGradient:
                 self.stats.recompute_steps += self.K - 1
                 flip = self.L.adjoint_chain(states, cur, nxt)
             else:
-                # recompute the K steps of the segment keeping only their moments
-                moms = [self.moms[j] for j in range(self.K)]
-                self.L.record_moments(self.ckpts[s], self.work[0], self.work[1], moms)
-                self.stats.recompute_steps += self.K
+                # recompute the K steps of the segment keeping only their moments (the last
+                # segment's were recorded by the forward)
+                sets = self.moms_sets
+                moms = [sets[s % len(sets)][j] for j in range(self.K)]
+                if s < self.N // self.K - self.n_taped:
+                    self.L.record_moments(self.ckpts[s], self.work[0], self.work[1], moms)
+                    self.stats.recompute_steps += self.K
                 flip = self.L.adjoint_chain_moments(moms, cur, nxt)
             if flip == 1:
                 cur, nxt = nxt, cur
@@ -202,24 +227,35 @@ class WidthGradient:
         rec.wait_stream(main)                     # the checkpoints and lam_N are written on main
 
         def record(s):
-            moms = self.moms_sets[s % 2]
-            if s + 2 < S:
-                rec.wait_event(ev_adj[s + 2])     # its record set was read by the adjoint of s + 2
+            moms = self.moms_sets[s % nset]
+            if s + nset < S:
+                rec.wait_event(ev_adj[s + nset])  # its record set was read by the adjoint of s + nset
             self.Lrec.record_moments(self.ckpts[s], self.work[0], self.work[1], [moms[j] for j in range(self.K)])
             ev_rec[s].record(rec)
             self.stats.recompute_steps += self.K
 
-        record(S - 1)
+        nset = len(self.moms_sets)
+        first_rec = S - 1 - self.n_taped      # segments above it were recorded by the forward
+        pending = [first_rec]                 # next segment to recompute (descending)
+
+        def issue_records(limit):
+            # every recompute down to segment `limit` whose set's last reader (the adjoint of
+            # r + nset) has been issued, so that its event wait is ordered after that record
+            while pending[0] >= 0 and pending[0] >= limit:
+                record(pending[0])
+                pending[0] -= 1
+
+        issue_records(S - nset)
         for s in range(S - 1, -1, -1):
-            main.wait_event(ev_rec[s])
-            moms = self.moms_sets[s % 2]
+            if s <= first_rec:
+                main.wait_event(ev_rec[s])
+            moms = self.moms_sets[s % nset]
             flip = self.L.adjoint_chain_moments([moms[j] for j in range(self.K)], cur, nxt)
             ev_adj[s].record(main)
             if flip == 1:
                 cur, nxt = nxt, cur
             self.stats.adjoint_steps += self.K
-            if s > 0:
-                record(s - 1)
+            issue_records(s - nset)
         return cur
 
     def close(self):

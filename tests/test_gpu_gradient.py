@@ -102,11 +102,35 @@ def test_moment_store_gives_the_same_gradient(adj):
         if store == "tape":
             assert drv.stats.recompute_steps == 0 and drv.stats.adjoint_steps == 60
             assert drv.stats.checkpoint_bytes == 0
+        if store == "moments":
+            # the forward records its last segments itself, one per record set (one without
+            # the overlap, four by default with it); the backward recomputes only the others
+            assert drv.n_taped == min(len(drv.moms_sets), 3) == (3 if pipe else 1)
+            assert drv.stats.recompute_steps == 20 * (3 - drv.n_taped)
         drv.close()
     for val, g, gp in out[1:]:
         assert val == out[0][0]
         np.testing.assert_array_equal(g, out[0][1])
         np.testing.assert_array_equal(gp, out[0][2])
+
+
+@pytest.mark.parametrize("nsteps,ckpt", [(40, 20), (20, 20), (30, 10)])
+def test_moment_store_segment_counts(adj, nsteps, ckpt):
+    """With one, two or three segments the moment store (the forward recording the moments of
+    the segments the backward reads first, one per record set) gives the state store's
+    gradient bit for bit, with and without the overlap and with more record sets."""
+    lat = W.Lattice(24, 72, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=27)
+    m = lat.modes()
+    out = []
+    for store, pipe, nset in (("states", False, None), ("moments", False, None), ("moments", True, None),
+                              ("moments", True, 3), ("moments", False, 2)):
+        drv = adj.WidthGradient(lat, nsteps, ckpt, store=store, pipeline=pipe, record_sets=nset)
+        val = drv.forward(m.amp_lo, m.amp_hi)
+        out.append((val, np.concatenate(drv.backward())))
+        drv.close()
+    for val, g in out[1:]:
+        assert val == out[0][0]
+        np.testing.assert_array_equal(g, out[0][1])
 
 
 def test_tape_store_refuses_other_precisions_and_walls(adj):
