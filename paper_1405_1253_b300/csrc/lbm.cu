@@ -218,7 +218,7 @@ struct lbm_ctx {
     // LBM_F32_DEV: the per-row reference (step_f32dev.cuh)
     double* fref = nullptr;     // Q * Lz: fref_l(z) (FP64)
     float* dref = nullptr;      // NDREF * Lz: gref_l(z) - fref_l(z) by (shell, c_z) class
-    float* rowc = nullptr;      // RC_N * Lz: per-row constants
+    float* rowc = nullptr;      // RC_N * Lz: per-row constants (RC_N per row)
 };
 
 static size_t pop_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64_FF) ? 8 : 4; }
@@ -403,7 +403,7 @@ static int dev_reference(lbm_ctx* c, const double* rho0, const double* T0) {
         const long double Tg = 0.5L * (r * r * eg - ug2);
         const float v[RC_N] = {(float)rho0[z], (float)((long double)T0[z] - 1.0L), (float)(R - rho0[z]),
                                (float)(Tg - T0[z]), (float)eg, (float)Jx, (float)Jz, (float)ug2};
-        for (int k = 0; k < RC_N; k++) h_rowc[(size_t)k * Lz + z] = v[k];
+        for (int k = 0; k < RC_N; k++) h_rowc[(size_t)z * RC_N + k] = v[k];
     }
     CU(cudaStreamSynchronize(c->stream));     // no step may read the tables while they change
     CU(cudaMemcpy(c->fref, h_fref.data(), h_fref.size() * sizeof(double), cudaMemcpyHostToDevice));
