@@ -44,6 +44,18 @@ struct EnsLattice {
 // them) were slower while every thread also held the lattice record in registers (6,657 and
 // 17,294); with the record in shared memory they are faster (ens_item_tile).
 constexpr int ens_item(bool) { return 8; }
+// Wall tiles per work item (a lattice's items: its wall tiles in items of ens_wall_item, then
+// its interior tiles in items of ens_item).  A float-float wall tile (six scattered rows with
+// the bounce-back rule) takes several times an interior tile; eight of them in one item made
+// that item the last of its lattice's step, which the next step's items of the lattice wait
+// for: wall tiles one per item took 16 lattices of 256x512 from 6,240 to 7,137 MLUPS (48-lattice
+// set unchanged, 7,368 / 7,360).  FP32 wall tiles are cheap, and single-tile items only add
+// queue work there (19,035 -> 18,742 and 19,410 -> 19,270): they keep 8.
+constexpr int ens_wall_item(bool ff) { return ff ? 1 : 8; }
+// Work items of a lattice with nwall wall tiles of ntiles.
+inline int ens_items(bool ff, int nwall, int ntiles) {
+    return (nwall + ens_wall_item(ff) - 1) / ens_wall_item(ff) + (ntiles - nwall + ens_item(ff) - 1) / ens_item(ff);
+}
 
 struct EnsControl {   // device words, reset before every persistent launch
     unsigned int queue;
@@ -227,12 +239,14 @@ k_ens_persistent(const EnsLattice* __restrict__ lats, int n, P q, int nsteps, in
                 const int s = (int)(it / (unsigned int)total_items);
                 const int j = (int)(it % (unsigned int)total_items);
                 const int i = ens_find_item(lats, n, j);
-                constexpr int KT = ens_item(std::is_same<P, StepParamsFF>::value);
+                constexpr bool FF = std::is_same<P, StepParamsFF>::value;
+                constexpr int KT = ens_item(FF), KW = ens_wall_item(FF);
                 s_L = lats[i];
                 s_i = i;
                 s_s = s;
-                s_t0 = (j - s_L.item_begin) * KT;
-                s_t1 = min(s_t0 + KT, s_L.ntiles);
+                const int local = j - s_L.item_begin, nw = s_L.t.nwall, nwi = (nw + KW - 1) / KW;
+                s_t0 = local < nwi ? local * KW : nw + (local - nwi) * KT;
+                s_t1 = local < nwi ? min(s_t0 + KW, nw) : min(s_t0 + KT, s_L.ntiles);
             }
         }
         __syncthreads();

@@ -1231,8 +1231,7 @@ static int ens_layout(lbm_ensemble* e) {
         L.ntiles = tiling_blocks(L.t);
         L.item_begin = ib;
         tb += L.ntiles;
-        const int kt = ens_item(e->prec == LBM_F64_FF);
-        ib += (L.ntiles + kt - 1) / kt;
+        ib += ens_items(e->prec == LBM_F64_FF, L.t.nwall, L.ntiles);
     }
     e->total_tiles = tb;
     e->total_items = ib;
