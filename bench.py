@@ -35,6 +35,11 @@ Q = 37
 METRIC = "MLUPS and % HBM roofline, FP64 vs FP32-storage (stated error), adjoint/forward"
 REF_BUDGET_S = 120.0        # oracle seconds of one reference-arm run (warmup + timed steps)
 SPEC_HBM_GBS = 7700.0       # nominal B300 HBM3e bandwidth (context beside the measured copy peak)
+# The paper's own throughput for this step (Table I, FP64, its D2Q37 RT code): context beside
+# the B300 numbers, not a target (other hardware, other code).
+PAPER_TABLE_I = [{"hardware": "NVIDIA C2050 (Fermi)", "mlups": 22.0, "precision": "f64"},
+                 {"hardware": "NVIDIA K20X (Kepler)", "mlups": 124.0, "precision": "f64"},
+                 {"hardware": "2x Intel Sandy Bridge", "mlups": 21.7, "precision": "f64"}]
 BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4, "f32_dev": 4}
 ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32", "f32_dev": "f32"}
 KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32", "f32_dev": "k_step_f32dev"}
@@ -673,7 +678,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": ARITH[prec],
         "data": "synthetic (seeded three-layer Rayleigh-Taylor initial state)",
         "config": {"workload": "three-layer RT, D2Q37, 1024x2048, tau=0.7, g=5e-5, 64 modes",
-                   "Lx": lat.Lx, "Lz": lat.Lz, "storage": "f32" if prec == "f32" else "f64",
+                   "Lx": lat.Lx, "Lz": lat.Lz,
+                   "storage": {"f32": "f32", "f32_dev": "f32 deviation from a per-row f64 reference"}.get(prec, "f64"),
                    "arith": ARITH[prec], "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "working set 1.24 GB per step > 126 MB L2 (no flush needed)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -697,6 +703,8 @@ def run_ours(args):
         "variants": variants,
         "mass_after": mass,
         "cpu_baseline": cpu,
+        "paper_context": {"source": "the paper's Table I (FP64)", "note": "context, not the target",
+                          "figures": PAPER_TABLE_I},
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
