@@ -45,22 +45,24 @@ __device__ __forceinline__ void collide_f64(const double (&g)[Q], double (&fo)[Q
     const double a = r * ux, b = r * usz;          // s_l = c_x a + c_z b
     const double orho = p.omega * 0x1p-60 * R;
     fo[0] = fma(p.one_m_omega, g[0], orho * d_lat.w[0] * k00);    // rest population
+    // The shell factor W = w omega rho is folded into each shell's coefficients (formed once
+    // per shell), so that a pair costs s, s^2, two Horner steps per part and the relaxation.
     static_for<NPAIR>([&](auto k) {
         constexpr int A = pair_first(decltype(k)::value), B = opp(A);
         constexpr int SH = shell_of(A);
         constexpr double C2 = (double)c2(A);
-        const double K0 = fma(C2, fma(C2, k02, k01), k00);
-        const double K1 = fma(C2, k11, k10);
-        const double K2 = fma(C2, k21, k20);
+        const double W = orho * d_lat.w[SH];
+        const double WK0 = W * fma(C2, fma(C2, k02, k01), k00);
+        const double WK1 = W * fma(C2, k11, k10);
+        const double WK2 = W * fma(C2, k21, k20);
+        const double W24 = W * (1.0 / 24.0), W6 = W * (1.0 / 6.0);
         double s;
         if constexpr (cx(A) == 0) s = (double)cz(A) * b;
         else if constexpr (cz(A) == 0) s = (double)cx(A) * a;
         else s = fma((double)cx(A), a, (double)cz(A) * b);
         const double s2 = s * s;
-        const double Ev = fma(s2, fma(s2, 1.0 / 24.0, K2), K0);
-        const double Od = s * fma(s2, 1.0 / 6.0, K1);
-        const double W = orho * d_lat.w[SH];
-        const double Pa = W * Ev, Pb = W * Od;
+        const double Pa = fma(s2, fma(s2, W24, WK2), WK0);             // W x even part
+        const double Pb = s * fma(s2, W6, WK1);                         // W x odd part
         fo[A] = fma(p.one_m_omega, g[A], Pa + Pb);
         fo[B] = fma(p.one_m_omega, g[B], Pa - Pb);
     });
