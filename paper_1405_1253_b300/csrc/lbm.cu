@@ -1314,6 +1314,7 @@ int lbm_ensemble_create(lbm_ensemble** out, int n, lbm_ctx* const* ctxs) {
             return fail(LBM_EINVAL, "context %d differs from context 0 in device, precision, tau, g or stream", i);
         NEED_BOUNCE_BACK(b, "an ensemble");
     }
+    NOT_DEV(ctxs[0], "an ensemble");
     if (ctxs[0]->prec != LBM_F64_FF && ctxs[0]->prec != LBM_F32)
         return fail(LBM_EINVAL, "ensembles take LBM_F64_FF or LBM_F32 contexts");
     DeviceGuard dg(ctxs[0]->device);

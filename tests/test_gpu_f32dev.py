@@ -133,7 +133,7 @@ def test_refusals(lbm):
     out = f.clone()
     calls = [lambda: L.adjoint_step(f, lam, out), lambda: L.step_push(1), lambda: L.propagate(),
              lambda: L.set_walls(True, lat.T_d, lat.T_u), lambda: lbm.Slabs(L, 2),
-             lambda: L.adjoint_chain([f, f], lam, out)]
+             lambda: L.adjoint_chain([f, f], lam, out), lambda: lbm.Ensemble([L])]
     for call in calls:
         with pytest.raises(lbm.LBMError) as e:
             call()
