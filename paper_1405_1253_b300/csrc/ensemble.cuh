@@ -49,9 +49,12 @@ constexpr int ens_item(bool) { return 8; }
 // the bounce-back rule) takes several times an interior tile; eight of them in one item made
 // that item the last of its lattice's step, which the next step's items of the lattice wait
 // for: wall tiles one per item took 16 lattices of 256x512 from 6,240 to 7,137 MLUPS (48-lattice
-// set unchanged, 7,368 / 7,360).  FP32 wall tiles are cheap, and single-tile items only add
-// queue work there (19,035 -> 18,742 and 19,410 -> 19,270): they keep 8.
-constexpr int ens_wall_item(bool ff) { return ff ? 1 : 8; }
+// set unchanged, 7,368 / 7,360), two per item to 7,202-7,216 (one per item on the same box:
+// 7,063-7,071; the 48-lattice set still unchanged).  FP32 wall tiles are cheap, and single-tile
+// items only add queue work there (19,035 -> 18,742 and 19,410 -> 19,270): they keep 8.  Larger
+// interior items (12 or 16 tiles) gained 0.2% on the 48-lattice set and lost 13% and 23% on the
+// 16 small lattices.
+constexpr int ens_wall_item(bool ff) { return ff ? 2 : 8; }
 // Work items of a lattice with nwall wall tiles of ntiles.
 inline int ens_items(bool ff, int nwall, int ntiles) {
     return (nwall + ens_wall_item(ff) - 1) / ens_wall_item(ff) + (ntiles - nwall + ens_item(ff) - 1) / ens_item(ff);
