@@ -133,6 +133,14 @@ def test_moment_store_segment_counts(adj, nsteps, ckpt):
         np.testing.assert_array_equal(g, out[0][1])
 
 
+def test_record_sets_need_two_with_the_overlap(adj):
+    lat = W.Lattice(8, 24, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=26)
+    with pytest.raises(ValueError):
+        adj.WidthGradient(lat, 4, 2, store="moments", pipeline=True, record_sets=1)
+    with pytest.raises(ValueError):
+        adj.WidthGradient(lat, 4, 2, store="moments", pipeline=False, record_sets=0)
+
+
 def test_tape_store_refuses_other_precisions_and_walls(adj):
     lat = W.Lattice(8, 24, tau=0.8, grav=1e-4, K=2, sigma=1.0, seed=26)
     for kw in ({"prec": "f64"}, {"prec": "f32"}, {"walls": (1.02, 0.98)}):
