@@ -1,5 +1,5 @@
 """Parity at full size, in the launch configuration the benchmark times: the largest
-configuration (4096 x 8192), the adjoint step (from the state and from a moment record) and
+configuration (4096 x 8192, float-float and FP32 deviation storage), the adjoint step (from the state and from a moment record) and
 the thermal walls on 1024 x 2048, compared on sampled columns against the oracle run on a
 periodic window of columns around each (wide enough to hold the column's dependence cone).
 Windows are cut on the device, so no full state crosses to the host."""
@@ -69,6 +69,27 @@ def test_largest_configuration_4096x8192_sampled_columns(env):
         ref = oracle.step(window(torch, f0, lat.Lx, lat.Lz, x0, 6), lat.tau, lat.grav, 2)[:, 6, :]
         got = column(torch, f2, lat.Lx, lat.Lz, x0)
         assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-13
+    del f0, f2
+    L.close()
+    torch.cuda.empty_cache()
+
+
+def test_deviation_storage_4096x8192_sampled_columns(env):
+    """The FP32 deviation storage on the precision configuration (reference from the initial
+    rows' means): 2 steps against the oracle on 13-column windows of the FP64 state the
+    context holds (f_ref + d).  Each step adds up to ~16 units of 2^-24 |d| / f (|d| <= 30% of
+    f), so 2 steps stay below 2 * 16 * 2^-24 * 0.3 = 5.7e-7 per population."""
+    torch, lbm = env
+    lat = W.PRECISION_4096x8192
+    L = lbm.Lattice(lat.Lx, lat.Lz, lat.tau, lat.grav, prec="f32_dev")
+    L.init_from(lat)
+    f0 = L.populations_device()
+    L.step(2)
+    f2 = L.populations_device()
+    for x0 in (0, 2047, 4095):
+        ref = oracle.step(window(torch, f0, lat.Lx, lat.Lz, x0, 6), lat.tau, lat.grav, 2)[:, 6, :]
+        got = column(torch, f2, lat.Lx, lat.Lz, x0)
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 5.7e-7
     del f0, f2
     L.close()
     torch.cuda.empty_cache()
