@@ -95,12 +95,12 @@ typedef struct {
 
 /* Create a context for an Lx x Lz lattice with relaxation time tau > 0.5 and gravity
  * g >= 0 (Sec. III.A).  buf0 and buf1 are 16-byte aligned device buffers on one device
- * of at least 37*Lx*Lz*(8 for LBM_F64 / LBM_F64_FF, 4 for LBM_F32) bytes
+ * of at least 37*Lx*Lz*(8 for LBM_F64 / LBM_F64_FF, 4 for LBM_F32 / LBM_F32_DEV) bytes
  * each, `bytes` the size of each; they hold the two lattice copies (Sec. III.B: read
  * one, write the other, swap).  The state starts in buf0.  cuda_stream is a
  * cudaStream_t (NULL: the legacy default stream).  The context allocates only small
- * private scratch (reduction partials, mode parameters, an error word).  On
- * failure *out is NULL.                                                               */
+ * private scratch (reduction partials, mode parameters, an error word; for LBM_F32_DEV
+ * also the reference tables, 37*Lz doubles and 26*Lz floats).  On failure *out is NULL.  */
 int lbm_create(lbm_ctx **out, int Lx, int Lz, int prec, double tau, double g,
                void *buf0, void *buf1, size_t bytes, void *cuda_stream);
 
@@ -157,7 +157,8 @@ void *lbm_current(lbm_ctx *c);
 
 /* Copy the current state out / in as canonical FP64 f[l][x][z] (37*Lx*Lz doubles).
  * on_device = 1: `f` is a device pointer (stream-ordered, asynchronous); 0: a host
- * pointer (the call synchronises).  FP32 storage is converted.                        */
+ * pointer (the call synchronises).  FP32 storage is converted; LBM_F32_DEV adds (in) or
+ * subtracts (out) the context's reference f_ref(l, z) in FP64 and rounds the deviation.   */
 int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
 int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
 
