@@ -157,8 +157,8 @@ void *lbm_current(lbm_ctx *c);
 
 /* Copy the current state out / in as canonical FP64 f[l][x][z] (37*Lx*Lz doubles).
  * on_device = 1: `f` is a device pointer (stream-ordered, asynchronous); 0: a host
- * pointer (the call synchronises).  FP32 storage is converted; LBM_F32_DEV adds (in) or
- * subtracts (out) the context's reference f_ref(l, z) in FP64 and rounds the deviation.   */
+ * pointer (the call synchronises).  FP32 storage is converted; LBM_F32_DEV copies out
+ * f_ref(l, z) + d in FP64 and stores (float)(f - f_ref(l, z)) on the way in.              */
 int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
 int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
 
