@@ -214,10 +214,12 @@ class WidthGradient:
         return g_lo, g_hi
 
     def _backward_pipelined(self, cur, nxt):
-        """The moment-record backward with the recompute of segment s - 1 (recording context,
-        second stream) overlapping the adjoint chain of segment s (the context's stream).  The
-        adjoint of s waits for the records of s; the recompute of s - 1 reuses the record set
-        of s + 1, so it waits for that segment's adjoint.  Returns the tensor holding lam_0."""
+        """The moment-record backward with the recomputes of earlier segments (recording
+        context, second stream) overlapping the adjoint chains (the context's stream), n record
+        sets: the adjoint of s waits for the records of s (recorded by the forward for the last
+        n segments); the recompute of r refills set r mod n, so it waits for the adjoint of
+        r + n, the set's last reader, and is issued right after that adjoint is (a stream must
+        not wait on an event before its record is enqueued).  Returns the tensor holding lam_0."""
         torch = self.torch
         S = self.N // self.K
         main = self.L.stream
