@@ -393,6 +393,15 @@ int lbm_test_fail_alloc(int n);
  * counterpart.                                                                          */
 int lbm_test_packed_ff(int n, unsigned long long seed, unsigned long long *mismatches);
 
+/* Throughput of the current device's FP64 pipe, the second roof of the FP64-storage steps
+ * (their FP64 instructions per site against it, beside their DRAM bytes per site against the
+ * HBM bandwidth): two launches of 8 blocks of 256 threads per SM, each thread running 8
+ * independent chains of iters FMAs; the second launch is timed with CUDA events on the
+ * legacy default stream.  *fma_per_s = thread-level FP64 FMAs per second.  Synchronises
+ * the device.  LBM_EINVAL for iters outside 1 .. 2^18 or a NULL pointer.  The paper has no
+ * counterpart.                                                                          */
+int lbm_probe_fp64_rate(int iters, double *fma_per_s);
+
 /* Message of the last failed call on this thread ("" if none).                        */
 const char *lbm_last_error(void);
 

@@ -28,6 +28,7 @@
 #include "adjoint_walls.cuh"
 #include "ensemble.cuh"
 #include "selftest.cuh"
+#include "probe.cuh"
 
 using namespace lbm;
 
@@ -447,6 +448,40 @@ int lbm_test_packed_ff(int n, unsigned long long seed, unsigned long long* misma
     if (e == cudaSuccess) e = cudaMemcpy(mismatches, d, sizeof *d, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "packed float-float self-test: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_probe_fp64_rate(int iters, double* fma_per_s) {
+    if (iters < 1 || iters > (1 << 18) || !fma_per_s)
+        return fail(LBM_EINVAL, "iters = %d (1 .. 2^18), fma_per_s %p", iters, (void*)fma_per_s);
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double* d = nullptr;
+    if (dev_malloc(&d, sizeof *d) != cudaSuccess) return fail(LBM_ENOMEM, "cannot allocate the probe's word");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = sms * PROBE_BLOCKS_PER_SM;
+    float ms = 0.0f;
+    if (e == cudaSuccess) {
+        k_probe_dfma<<<blocks, PROBE_THREADS>>>(iters, 0.999999, 1e-6, d);    // warm-up
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0);
+    if (e == cudaSuccess) {
+        k_probe_dfma<<<blocks, PROBE_THREADS>>>(iters, 0.999999, 1e-6, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "FP64 probe: %s", cudaGetErrorString(e));
+    if (!(ms > 0.0f)) return fail(LBM_ECUDA, "FP64 probe: no elapsed time");
+    *fma_per_s = (double)blocks * PROBE_THREADS * PROBE_CHAINS * (double)iters / (ms * 1e-3);
     return LBM_OK;
 }
 

@@ -83,6 +83,7 @@ _SIGS = {
     "lbm_test_fail_alloc": (_i, [_i]),
     "lbm_test_packed_ff": (_i, [_i, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong)]),
     "lbm_test_oob_count": (_i, [ctypes.POINTER(ctypes.c_uint)]),
+    "lbm_probe_fp64_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double)]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -102,6 +103,13 @@ def test_packed_ff(n: int, seed: int) -> int:
     n seeded operand pairs (lbm_test_packed_ff)."""
     out = ctypes.c_ulonglong(0)
     _check(_lib.lbm_test_packed_ff(int(n), ctypes.c_ulonglong(seed), ctypes.byref(out)))
+    return out.value
+
+
+def probe_fp64_rate(iters: int = 2048) -> float:
+    """FP64 FMAs per second of the current device's FP64 pipe (lbm_probe_fp64_rate)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.lbm_probe_fp64_rate(int(iters), ctypes.byref(out)))
     return out.value
 
 
