@@ -43,11 +43,13 @@ PAPER_TABLE_I = [{"hardware": "NVIDIA C2050 (Fermi)", "mlups": 22.0, "precision"
 BYTES_PER_POP = {"f64": 8, "f64_ff": 8, "f32": 4, "f32_dev": 4}
 ARITH = {"f64": "f64", "f64_ff": "f64+f32x2", "f32": "f32", "f32_dev": "f32"}
 KERNEL = {"f64": "k_step_f64", "f64_ff": "k_step_ff", "f32": "k_step_f32", "f32_dev": "k_step_f32dev"}
-# FP64-pipe instructions per site update, counted from the kernels' source: the float-float
-# step converts its four integer moment sums to binary64 and makes one FMA for T - 1 and one
-# per population; its adjoint adds one binary64 add per population but the rest one.
+# FP64-pipe instructions per site update.  The float-float step converts its four integer
+# moment sums to binary64 and makes one FMA for T - 1 and one per population; its adjoint adds
+# one binary64 add per population but the rest one (ncu's thread-level FP64-pipe instruction
+# count per site, sm__thread_inst_executed_pipe_fp64_pred_on, gives the same 42 and 78).  The
+# native FP64 step's count is ncu's alone: 174 FMAs, 86 multiplies, 17 adds, 4 conversions.
 FP64_INSTR_PER_SITE = {"k_step_ff": 4 + 1 + Q, "k_adjoint_ff": 4 + 1 + Q + (Q - 1),
-                       "k_adjoint_ff_moments": 4 + 1 + Q + (Q - 1)}
+                       "k_adjoint_ff_moments": 4 + 1 + Q + (Q - 1), "k_step_f64": 281}
 
 
 def fp64_roof(kernel, sites, ms, rate):
@@ -667,6 +669,9 @@ def run_ours(args):
             vbytes = 2 * Q * BYTES_PER_POP[v] * sites
             variants[v] = {"mlups": sites / (vms * 1e-3) / 1e6, "ms_per_step": vms,
                            "gbs": vbytes / (vms * 1e-3) / 1e9, "arith": ARITH[v]}
+            roof = fp64_roof(KERNEL[v], sites, vms, fp64_rate)
+            if roof is not None:
+                variants[v]["fp64"] = roof
 
     extras = {}
     if not args.no_extras and rank == 0:

@@ -397,7 +397,8 @@ int lbm_test_packed_ff(int n, unsigned long long seed, unsigned long long *misma
  * (their FP64 instructions per site against it, beside their DRAM bytes per site against the
  * HBM bandwidth): two launches of 8 blocks of 256 threads per SM, each thread running 8
  * independent chains of iters FMAs; the second launch is timed with CUDA events on the
- * legacy default stream.  *fma_per_s = thread-level FP64 FMAs per second.  Synchronises
+ * legacy default stream.  *fma_per_s = thread-level FP64 FMAs per second (a pure FP64
+ * stream: kernels that mix FP64 with other work can run the pipe about 5% faster).  Synchronises
  * the device.  LBM_EINVAL for iters outside 1 .. 2^18 or a NULL pointer.  The paper has no
  * counterpart.                                                                          */
 int lbm_probe_fp64_rate(int iters, double *fma_per_s);
