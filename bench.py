@@ -616,8 +616,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     warm_ms_step = e0.elapsed_time(e1) / args.warmup
     # the FP64 pipe's rate on this GPU, the second roof of the FP64-storage step (outside the
-    # timed region; about 20 ms)
-    fp64_rate = lbm.probe_fp64_rate()
+    # timed region; two launches of about 2.6 ms)
+    fp64_rate = lbm.probe_fp64_rate(512)
 
     def barrier():
         if ws > 1:
