@@ -99,3 +99,16 @@ def test_traffic_records_follow_code_not_comments():
     b = "// f\nint f(int x) {\n  return 2 * x;\n}"
     c = "int f(int x) { return 3 * x; }"
     assert bench.code_of(a) == bench.code_of(b) != bench.code_of(c)
+
+
+def test_fp64_roof():
+    """The second roof: FP64 instructions per site x sites per second against the probe's rate;
+    no figure for a kernel without a stated count or without a measured rate."""
+    import bench
+    r = bench.fp64_roof("k_step_ff", 2_000_000, 0.5, 4e11)
+    assert r["instr_per_site"] == 42 and r["bound"] == "fp64_pipe"
+    assert r["achieved"] == pytest.approx(42 * 2e6 / 0.5e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 400.0)
+    assert bench.fp64_roof("k_adjoint_ff", 1, 1.0, 1e9)["instr_per_site"] == 78
+    assert bench.fp64_roof("k_step_f32", 1, 1.0, 1e9) is None
+    assert bench.fp64_roof("k_step_ff", 1, 1.0, None) is None
