@@ -4,6 +4,7 @@ the adjoint step to a seeded random field at the final state (in the storage pre
   python -m paper_1405_1253_b300.run --prec f64_ff --Lx 1024 --Lz 2048 --steps 3
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 1 --adjoint 3 [--store moments]
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 3 --walls      (thermal walls)
+  python -m paper_1405_1253_b300.run --prec f64_ff --steps 3 --push       (push form)
   python -m paper_1405_1253_b300.run --prec f64_ff --steps 20 --ensemble 16 --ens-mode 1
       (the first 16 lattices of the 48-lattice ensemble: --steps steps in one launch per step
        (--ens-mode 0) or one persistent launch (1), tile height 128)
@@ -33,6 +34,8 @@ def main():
     ap.add_argument("--store", default="states", choices=["states", "moments"],
                     help="the adjoint reads the state (gathers f_t) or a moment record of the step")
     ap.add_argument("--walls", action="store_true", help="thermal walls at the bottom and top layer temperatures")
+    ap.add_argument("--push", action="store_true",
+                    help="push form: one propagate into the push convention, then --steps push steps")
     ap.add_argument("--ensemble", type=int, default=0, help="run the first N lattices of the 48-lattice ensemble")
     ap.add_argument("--ens-mode", type=int, default=1, choices=[0, 1],
                     help="0: one launch per step, 1: one persistent launch")
@@ -57,11 +60,15 @@ def main():
     L.init_from(lat)
     if args.walls:
         L.set_walls(True, lat.T_d, lat.T_u)
-    L.step(args.steps)
+    if args.push:
+        L.propagate()
+        L.step_push(args.steps)
+    else:
+        L.step(args.steps)
     L.sync()
     mass, energy = L.global_sums()
     out = {"prec": args.prec, "Lx": lat.Lx, "Lz": lat.Lz, "steps": args.steps, "walls": args.walls,
-           "mass": mass, "energy": energy}
+           "push": args.push, "mass": mass, "energy": energy}
     if args.adjoint > 0:
         import torch
         f = L.current().clone()                   # the state in the storage precision
